@@ -1,0 +1,133 @@
+"""Exact steady-state distribution of a small PBN with perturbations.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Builds the full 2^n x 2^n transition matrix P of the DTMC underlying a PBN
+(Sec. 2.1-2.2) and runs FP64 power iteration pi <- pi P from the uniform
+distribution until the L1 change drops below a tolerance; an ergodic DTMC's
+limiting distribution does not depend on the start (Sec. 2.1).  State index
+s = sum_i v_i 2^i.
+
+The probabilities are the quantised ones the simulation realises exactly:
+perturbation probability P32/2^32 and function probabilities
+(T_j - T_{j-1})/2^32 (see oracle.c for the definition of P32 and T_j).  This
+module recomputes that quantisation in Python on its own, so that comparing it
+with the C simulator checks both.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+TWO32 = 4294967296
+
+
+def _llround_pos(x: float) -> int:
+    q = math.floor(x)
+    if x - q >= 0.5:
+        q += 1
+    return int(q)
+
+
+def perturb_threshold(p: float) -> int:
+    return max(0, min(_llround_pos(p * 4294967296.0), TWO32 - 1))
+
+
+def category_probabilities(net):
+    """Returns (p_pert, probs) where probs[f] = P(category of f) unconditionally
+    (u uniform on [0, 2^32)), and p_pert = P32 / 2^32."""
+    P32 = perturb_threshold(net.p)
+    span = TWO32 - P32
+    probs = np.zeros(net.n_functions, dtype=np.float64)
+    for i in range(net.n):
+        f0, f1 = int(net.fn_offset[i]), int(net.fn_offset[i + 1])
+        S = 0.0
+        prev = P32
+        for f in range(f0, f1):
+            S += float(net.select_prob[f])
+            if f == f1 - 1:
+                T = TWO32
+            else:
+                q = min(max(_llround_pos(float(span) * S), 0), span)
+                T = min(P32 + q, TWO32 - 1)
+            probs[f] = (T - prev) / TWO32
+            prev = T
+    return P32 / TWO32, probs
+
+
+def function_values(net, states: np.ndarray) -> np.ndarray:
+    """vals[s, f] = value of function f on state s (truth-table lookup)."""
+    S = len(states)
+    vals = np.zeros((S, net.n_functions), dtype=np.uint8)
+    for f in range(net.n_functions):
+        par = net.parents_of(f)
+        idx = np.zeros(S, dtype=np.int64)
+        for m, v in enumerate(par):
+            idx |= ((states >> int(v)) & 1) << m
+        vals[:, f] = (int(net.truth_table[f]) >> idx) & 1
+    return vals
+
+
+def transition_matrix(net, mode: int = 0) -> np.ndarray:
+    """Dense P for n <= 12.  mode 0: per-node perturbation; mode 1: global
+    (s XOR gamma when gamma != 0, functions otherwise)."""
+    n = net.n
+    if n > 12:
+        raise ValueError("dense transition matrix only for n <= 12")
+    S = 1 << n
+    states = np.arange(S, dtype=np.int64)
+    p_e, probs = category_probabilities(net)
+    vals = function_values(net, states)
+    # q[s, i] = P(next value of node i is 1 | s) for the function part
+    qf = np.zeros((S, n), dtype=np.float64)
+    for i in range(n):
+        for f in net.functions_of(i):
+            qf[:, i] += probs[f] * vals[:, f]
+    bits = ((states[:, None] >> np.arange(n)[None, :]) & 1).astype(np.float64)
+
+    def product_rows(q):
+        R = np.ones((S, 1), dtype=np.float64)
+        for i in range(n):
+            V = np.stack([1.0 - q[:, i], q[:, i]], axis=1)  # [S, 2]
+            R = (V[:, :, None] * R[:, None, :]).reshape(S, -1)
+        return R
+
+    if mode == 0:
+        q = p_e * (1.0 - bits) + qf
+        return product_rows(q)
+    # global: conditional on no perturbation the function of node i is chosen
+    # with probability probs[f] / (1 - p_e)
+    qc = qf / (1.0 - p_e) if p_e < 1.0 else qf
+    P = (1.0 - p_e) ** n * product_rows(qc)
+    h = np.array([bin(x).count("1") for x in range(S)], dtype=np.int64)
+    flip = np.where(h > 0, p_e ** h * (1.0 - p_e) ** (n - h), 0.0)  # by XOR pattern
+    P += flip[states[:, None] ^ states[None, :]]
+    return P
+
+
+def stationary_power(P: np.ndarray, tol: float = 1e-14, max_iter: int = 2_000_000):
+    """FP64 power iteration from the uniform distribution.  Returns (pi, iters)."""
+    S = P.shape[0]
+    pi = np.full(S, 1.0 / S)
+    for it in range(1, max_iter + 1):
+        nxt = pi @ P
+        delta = float(np.abs(nxt - pi).sum())
+        pi = nxt
+        if delta < tol:
+            return pi, it
+    raise RuntimeError("power iteration did not converge")
+
+
+def soi_mask(n: int, soi) -> np.ndarray:
+    states = np.arange(1 << n, dtype=np.int64)
+    m = np.ones(1 << n, dtype=bool)
+    for v, val in zip(soi.nodes, soi.values):
+        m &= ((states >> int(v)) & 1) == int(val)
+    return m
+
+
+def steady_state_probability(net, soi, mode: int = 0, tol: float = 1e-14):
+    P = transition_matrix(net, mode)
+    pi, _ = stationary_power(P, tol)
+    return float(pi[soi_mask(net.n, soi)].sum()), pi
