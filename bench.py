@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of the parallel steady-state method on one GB300.
+
+One step = one whole query of the hot path on the mid-size workload
+(n = 100 nodes, 2 functions per node, 2-5 parents, p = 0.001, 1024 chains,
+5-node state of interest): chain initialisation, the Gelman & Rubin burn-in
+(Alg. GR, R-hat < 1.05) and the parallel two-state Markov chain approach
+(Alg. 3, r = 0.005, s = 0.95, eps = 1e-10) up to the estimate.  Each step uses
+its own seed.  The metric is chain-node updates per second (omega x chain
+length x n over the query time), with the p50/p99 query latency beside it.
+
+Timing: CUDA events on the query's stream around every step, W warm-up steps
+first; L2 is flushed (a 256 MB write) between timed steps, outside the events.
+`e2e` repeats the measurement through the C ABI with the network's CSR arrays
+in pinned host memory copied to the device inside the timed region.
+
+--impl reference times the CPU oracle (single-threaded C) on bounded samples
+of the same workload (the simulation of all 1024 chains for a fixed number of
+transitions per step).
+
+Multi-GPU: the queries are independent, so N ranks run N replicas of the
+query stream (weak scaling); ranks only meet at the barriers and the final
+max-over-ranks of the timed region.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "chain-node updates/s"
+WORKLOAD = "mid-n100-omega1024-two-state-r0.005"
+PSI0 = 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    import pbn_synth as S
+    net, soi, cfg = S.mid_config()
+    return net, soi, cfg
+
+
+def config_dict(cfg, net):
+    return {"workload": WORKLOAD, "nodes": int(net.n), "functions": int(net.n_functions), "chains": cfg["omega"],
+            "p": net.p, "rhat_threshold": cfg["rhat"], "r": cfg["r"], "s": cfg["s"], "eps": cfg["eps"],
+            "psi0": PSI0, "state_of_interest": "nodes 0-4 = (1,0,1,1,0)", "perturbation": "per-node",
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- roofline
+
+def algorithmic_ops_per_item(net) -> np.ndarray:
+    """Integer operations the bit-sliced step needs for one (node, chain
+    group) item, per node, in expectation:
+      Philox4x32-10 blocks: 40 ops each (10 rounds x (2 wide multiplies +
+        2 three-input XORs)); blocks needed so that no lane of 32 is still tied
+        with one of the node's L category bounds: 1 + sum_b>=1 of
+        1 - (1 - min(1, L 2^-4b))^32;
+      digit comparison: 3 ops per bound per digit (4 digits per block);
+      function evaluation for each function some lane selects (probability
+        1 - (1 - c)^32): 2 ops per truth-table leaf, 1 per multiplexer,
+        1 load per parent: 3 * 2^k - 1 + k;
+      combine and store: 2 ops."""
+    ops = np.zeros(net.n)
+    for i in range(net.n):
+        fs = list(net.functions_of(i))
+        L = len(fs)
+        blocks = 1.0 + sum(1.0 - (1.0 - min(1.0, L * 2.0 ** (-4 * b))) ** 32 for b in range(1, 8))
+        o = blocks * (40 + 4 * 3 * L) + 2
+        for f in fs:
+            k = int(net.par_offset[f + 1] - net.par_offset[f])
+            c = float(net.select_prob[f])
+            o += (1.0 - (1.0 - c) ** 32) * (3 * (1 << k) - 1 + k)
+        ops[i] = o
+    return ops
+
+
+def alu_peak_tops(device_index):
+    """Issue-rate peak: SMs x 4 schedulers x 32 lanes x max SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
+    mhz = None
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        mhz = float(peaks.get("sm_max_mhz"))
+    except Exception:
+        pass
+    src = "MEASURED_PEAKS.json sm_max_mhz"
+    if not mhz:
+        try:
+            out = subprocess.check_output(["nvidia-smi", f"--id={device_index}", "--query-gpu=clocks.max.sm",
+                                           "--format=csv,noheader,nounits"], text=True)
+            mhz = float(out.strip().splitlines()[0]); src = "nvidia-smi clocks.max.sm"
+        except Exception:
+            mhz = 2070.0; src = "nominal 2070 MHz"
+    return sms * 4 * 32 * mhz * 1e6 / 1e12, sms, mhz, src
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_sample(net, soi, omega, target_s=12.0):
+    """Times the oracle simulating all `omega` chains of the workload network
+    for a number of transitions calibrated to about target_s seconds."""
+    import oracle
+    oracle.build()
+    st = oracle.init_states(net, 99, omega)
+    t = time.perf_counter()
+    oracle.simulate(net, 0, 99, st, 0, 2, soi)
+    per_step = (time.perf_counter() - t) / 2
+    steps = max(2, int(target_s / max(per_step, 1e-6)))
+    t = time.perf_counter()
+    oracle.simulate(net, 0, 99, st, 2, steps, soi)
+    dt = time.perf_counter() - t
+    upd = omega * steps * net.n
+    return upd / dt, steps, dt
+
+
+# ------------------------------------------------------------------- arms
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    net, soi, cfg = workload()
+    omega = cfg["omega"]
+    # one step = the oracle simulating all chains for a fixed number of
+    # transitions (about 4 s of CPU work)
+    _, calib_steps, _ = oracle_sample(net, soi, omega, target_s=0.5)
+    steps_per = max(2, calib_steps * 8)
+    st = oracle.init_states(net, 7, omega)
+    t0 = 0
+    for _ in range(args.warmup):
+        st, _ = oracle.simulate(net, 0, 7, st, t0, 2, soi)
+        t0 += 2
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        st, _ = oracle.simulate(net, 0, 7, st, t0, steps_per, soi)
+        times.append(time.perf_counter() - t)
+        t0 += steps_per
+    upd = omega * steps_per * net.n
+    value = upd * len(times) / sum(times)
+    sample = f"oracle simulation of all {omega} chains for {steps_per} transitions per step"
+    line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": config_dict(cfg, net), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+
+    net, soi, cfg = workload()
+    omega = cfg["omega"]
+    N = P.pbn_load(net)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    q = dict(omega=omega, psi0=PSI0, rhat=cfg["rhat"], eps=cfg["eps"], r=cfg["r"], s=cfg["s"])
+    seed0 = 1_000_000 * (rank + 1)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for w in range(args.warmup):
+        P.pbn_estimate_two_state(N, soi, seed=seed0 + 900_000 + w, **q)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, reports = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        rep = P.pbn_estimate_two_state(N, soi, seed=seed0 + k, **q)
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        reports.append(rep)
+    barrier()
+    clk = clocks.stop()
+
+    # e2e: host CSR arrays in pinned memory -> pbn_load -> query -> result on the host
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(net, k))).pin_memory()
+            for k in ("fn_offset", "par_offset", "parents", "truth_table", "select_prob")}
+    h2d = int(sum(v.numel() * v.element_size() for v in host.values()))
+    e2e_times, e2e_upd, e2e_d2h = [], 0, 0
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        Nk = P.pbn_load_pinned(host, net.n, net.p)
+        rep = P.pbn_estimate_two_state(Nk, soi, seed=seed0 + k, **q)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t)
+        Nk.close()
+        e2e_upd += rep["chain_node_updates"]
+        e2e_d2h += rep["d2h_bytes"]
+    barrier()
+
+    total_ms = sum(times)
+    upd = sum(r["chain_node_updates"] for r in reports)
+    e2e_s = sum(e2e_times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([upd, e2e_upd], dtype=torch.float64, device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_ms, e2e_s = float(t[0]), float(t[1])
+        upd_all, e2e_upd_all = float(u[0]), float(u[1])
+    else:
+        upd_all, e2e_upd_all = float(upd), float(e2e_upd)
+    if rank != 0:
+        return
+
+    value = upd_all / (total_ms / 1e3)
+    # roofline of the simulation kernel: algorithmic integer ops per launch
+    # over the event-timed launch durations of the timed region
+    ops_item = algorithmic_ops_per_item(net)
+    ops_per_group_step = float(ops_item.sum())
+    groups = (omega + 31) // 32
+    sim_ms = sum(r["sim_ms"] for r in reports)
+    sim_launches = sum(r["sim_launches"] for r in reports)
+    items = sum(r["sim_items"] for r in reports)
+    ops = ops_per_group_step * items / net.n
+    achieved = ops / (sim_ms / 1e3) / 1e12
+    peak, sms, mhz, peak_src = alu_peak_tops(local)
+    lat = sorted(times)
+    line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": config_dict(cfg, net),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(np.mean(lat))},
+            "queries_per_s": args.steps * world / (total_ms / 1e3),
+            "roofline": {"bound": "alu", "kernel": "sim_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"issue rate {sms} SMs x 128 lanes x {mhz:.0f} MHz ({peak_src})",
+                         "sim_share_of_step": sim_ms / total_ms,
+                         "ops_per_update": ops_per_group_step / net.n / 32,
+                         "launches": sim_launches, "avg_launch_ms": sim_ms / max(sim_launches, 1)},
+            "clocks": clk,
+            "e2e": {"value": e2e_upd_all / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": e2e_d2h // max(args.steps, 1)},
+            "gpu_launches": int(sum(r["kernel_launches"] for r in reports)),
+            "query": {"mean_length": float(np.mean([r["length"] for r in reports])),
+                      "mean_sample_size": float(np.mean([r["sample_size"] for r in reports])),
+                      "mean_prob": float(np.mean([r["prob"] for r in reports]))}}
+    if world == 1 and not args.no_cpu_baseline:
+        v, steps, dt = oracle_sample(net, soi, omega)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                                "sample": f"oracle simulation of all {omega} chains for {steps} transitions "
+                                          f"({dt:.1f} s)"}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

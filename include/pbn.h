@@ -1,0 +1,269 @@
+/*
+ * pbn.h -- C ABI of the GB300 (sm_103a) engine for approximate steady-state
+ * analysis of probabilistic Boolean networks (PBNs) by many parallel Markov
+ * chains, after Mizera, Pang & Yuan, "Parallel Approximate Steady-state
+ * Analysis of Large Probabilistic Boolean Networks".
+ *
+ * Conventions for every entry point:
+ *   - The return value is a pbn_status.  No C++ exception crosses this ABI.
+ *     On failure pbn_last_error() returns a thread-local message.
+ *   - Pointers documented as "device" must point to CUDA device memory of the
+ *     current device; "host" pointers to ordinary host memory.  The caller
+ *     owns every buffer it passes in; the library never frees or keeps them.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
+ *     is stream-ordered on it.  Entry points that return results in host
+ *     memory synchronise the stream before returning; the others do not.
+ *   - The library owns pbn_net handles (device copies of the network tables).
+ *
+ * Chain layout (bit-sliced, 32 chains per 32-bit word):
+ *   chain c belongs to group g = c / 32 and lane c % 32.
+ *   state[g * n + i]: bit (c % 32) is the value of node i of chain c.
+ *   bits[g * bits_cap + j]: bit (c % 32) is the indicator of the state of
+ *   interest (meta state 1, Sec. 3.1) of chain c at trajectory position
+ *   bits_base + j.  Trajectory position q holds the state after transition q
+ *   (state q+1); the initial state is not a sample.
+ *   Bits of lanes >= omega in the last group are unspecified.
+ *
+ * Random numbers (the paper does not fix them): Philox4x32-10 keyed by the
+ * 64-bit seed; node i, transition t and chain group g address counters
+ * (i, t lo32, (t hi32 & 0xFFFFFF) | b << 24, g), b = 0..7; chain c's uniform
+ * u takes bit c % 32 of the 32 output words as its digits, most significant
+ * first.  Perturbation iff u < P32 = round(p 2^32); otherwise function j of
+ * node i is selected when T_{j-1} <= u < T_j, T the quantised cumulative
+ * selection probabilities.  Every trajectory is a pure function of
+ * (seed, chain, transition, node), so runs are replayable and resumable.
+ */
+#ifndef PBN_H
+#define PBN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pbn_status {
+    PBN_OK = 0,
+    PBN_ERR_INVALID = 1,        /* malformed argument or network */
+    PBN_ERR_OOM = 2,            /* device or host allocation refused */
+    PBN_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    PBN_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up */
+    PBN_ERR_NOT_CONVERGED = 5,  /* a stopping rule was not met within the length cap */
+    PBN_ERR_INSUFFICIENT = 6,   /* the window cannot give alpha and beta (no 0->1 or 1->0) */
+    PBN_ERR_UNSUPPORTED = 7     /* valid input beyond this build's limits */
+} pbn_status;
+
+enum { PBN_PERTURB_PER_NODE = 0, PBN_PERTURB_GLOBAL = 1 };
+
+/* Limits of this build. */
+#define PBN_MAX_NODES 4096          /* node ids are 12-bit in the device tables */
+#define PBN_MAX_PARENTS 5           /* truth tables are one 32-bit word */
+#define PBN_MAX_FUNCTIONS_PER_NODE 8
+#define PBN_MAX_SOI 32
+
+/*
+ * A PBN G(V,F) (Sec. 2.2) with perturbation probability p, in CSR form.  All
+ * arrays are host memory and are copied by pbn_load.
+ *   fn_offset   [n+1]  functions of node i are fn_offset[i] .. fn_offset[i+1]-1
+ *   par_offset  [F+1]  parents of function f are parents[par_offset[f] ..]
+ *   parents     [par_offset[F]]  node ids; parent m is bit m of the index
+ *   truth_table [F]    f(x) = bit (sum_m x_m 2^m) of truth_table[f]
+ *   select_prob [F]    c_j^(i); per node they sum to 1 (within 1e-9)
+ */
+typedef struct pbn_network_desc {
+    int32_t n;
+    int32_t n_functions;
+    const int32_t *fn_offset;
+    const int32_t *par_offset;
+    const int32_t *parents;
+    const uint32_t *truth_table;
+    const double *select_prob;
+    double p;
+} pbn_network_desc;
+
+typedef struct pbn_net pbn_net;
+
+typedef struct pbn_net_info {
+    int32_t n;
+    int32_t n_functions;
+    uint32_t perturb_threshold;   /* P32 */
+    int64_t table_bytes;          /* device bytes of the staged tables */
+} pbn_net_info;
+
+/* State of interest: meta state 1 = every listed node holds its value
+ * (Sec. 3.1).  Host arrays, 1 <= size <= PBN_MAX_SOI. */
+typedef struct pbn_soi {
+    int32_t size;
+    const int32_t *nodes;
+    const uint8_t *values;
+} pbn_soi;
+
+/* Caller-owned chain buffers (device memory) and their position bookkeeping. */
+typedef struct pbn_chains {
+    int64_t omega;          /* number of chains (>= 1) */
+    uint32_t *state;        /* device [ceil(omega/32) * n] */
+    uint32_t *bits;         /* device [ceil(omega/32) * bits_cap], may be NULL if bits_cap == 0 */
+    int64_t bits_cap;       /* positions per group held by `bits` */
+    int64_t bits_base;      /* trajectory position of column 0 */
+    int64_t length;         /* trajectory length L: `state` holds state L */
+} pbn_chains;
+
+typedef struct pbn_run_cfg {
+    uint64_t seed;
+    int32_t perturb_mode;   /* PBN_PERTURB_PER_NODE or PBN_PERTURB_GLOBAL */
+    pbn_soi soi;
+    int32_t groups_per_block;   /* 0 = automatic */
+    int32_t threads_per_block;  /* 0 = automatic */
+} pbn_run_cfg;
+
+/* ---------------------------------------------------------------- network */
+
+/* Validate and stage a PBN (Sec. 2.2) on the current device: quantises p and
+ * the selection probabilities (see above) and builds the device tables.
+ * Errors: PBN_ERR_INVALID (structure, probabilities), PBN_ERR_UNSUPPORTED
+ * (n, parents or functions per node beyond the limits), PBN_ERR_OOM. */
+int pbn_load(const pbn_network_desc *desc, pbn_net **out);
+void pbn_free(pbn_net *net);
+int pbn_net_get_info(const pbn_net *net, pbn_net_info *out);
+
+/* ----------------------------------------------------------------- chains */
+
+/* Initial states (state 0): any initial state is allowed (Sec. 2.2); node i of
+ * chain c is bit c % 32 of word 0 of Philox(i, 0xFFFFFFFF, 0xFFFFFFFF, g).
+ * Sets chains->length = 0.  Errors: PBN_ERR_INVALID, PBN_ERR_CUDA. */
+int pbn_init_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *chains, void *stream);
+
+/* Extend every chain by `steps` transitions (Sec. 2.2: synchronous update of
+ * all nodes, each node perturbed with probability p or updated by a predictor
+ * function drawn by its selection probabilities; "Extend all trajectories",
+ * Alg. GR / Alg. 3 / Alg. 4).  Writes the indicator bits of positions
+ * length .. length+steps-1 that fall at or after bits_base; the caller must
+ * have made bits_cap cover them.  chains->length += steps.
+ * Errors: PBN_ERR_INVALID (SOI, capacity), PBN_ERR_CUDA. */
+int pbn_run_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *chains, int64_t steps,
+                   void *stream);
+
+/* ------------------------------------------------------------- statistics */
+
+typedef struct pbn_gr_result {
+    double rhat;            /* +inf when W = 0 */
+    double W, B, sigma2;
+    uint64_t S1;            /* sum over chains of ones in the window */
+    uint64_t S2_lo, S2_hi;  /* sum of squares, 128-bit */
+} pbn_gr_result;
+
+/* Gelman & Rubin (Sec. 4.1, Alg. GR) on the window of positions
+ * [start, start+psi) of every chain's indicator: per-chain mean and sample
+ * variance (denominator psi-1), B, W, sigma^2 = (1-1/psi) W + B/psi,
+ * R-hat = sqrt(sigma^2 / W).  Computed on the device from exact integer sums.
+ * out: device pointer, written asynchronously.  Needs omega >= 2, psi >= 2. */
+int pbn_gelman_rubin(const pbn_chains *chains, int64_t start, int64_t psi, pbn_gr_result *out,
+                     void *stream);
+
+typedef struct pbn_two_state_result {
+    int64_t n00, n01, n10, n11;  /* transitions within chains, both ends in the window */
+    int64_t ones;                /* ones in the window */
+    double alpha, beta;          /* alpha = n01/(n00+n01), beta = n10/(n10+n11) */
+    double prob;                 /* ones / (omega * len) */
+    int64_t M, N;                /* Alg. 1 line 8 */
+    int32_t status;              /* PBN_OK, PBN_ERR_INSUFFICIENT or PBN_ERR_NOT_CONVERGED (alpha = beta = 1) */
+    int32_t pad;
+} pbn_two_state_result;
+
+/* Two-state Markov chain statistics (Sec. 3.1, Alg. 1 line 8, Alg. 3) of the
+ * merged window [start, start+len) of all chains: transition counts, alpha,
+ * beta, burn-in M = ceil(log(eps (a+b)/max(a,b)) / log|1-a-b|), sample size
+ * N = ceil(a b (2-a-b)/(a+b)^3 (Phi^-1((1+s)/2))^2 / r^2), estimate.  On the
+ * device; out is a device pointer written asynchronously. */
+int pbn_two_state(const pbn_chains *chains, int64_t start, int64_t len, double eps, double r, double s,
+                  pbn_two_state_result *out, void *stream);
+
+typedef struct pbn_skart_result {
+    double mean, var, skew, phi, A, H, ci_lo, ci_hi;
+    double vn_stat;          /* von Neumann statistic of the spaced batch means */
+    int32_t vn_pass;         /* randomness test passed */
+    int32_t pad;
+    int64_t batches;         /* omega * batches_per_chain */
+} pbn_skart_result;
+
+/* Skart batch statistics (Sec. 3.2, Alg. 2; parallel layout Fig. 2b, Alg. 4):
+ * every chain contributes batches_per_chain consecutive batches of kappa
+ * positions from `start`; computes the von Neumann randomness test on the
+ * spaced batch means (spacer `spacer`, size alpha_ran) and the skewness- and
+ * autoregression-adjusted CI of the nonspaced batch means at level
+ * 1 - alpha_ci.  out: device pointer, written asynchronously. */
+int pbn_skart(const pbn_chains *chains, int64_t start, int64_t kappa, int64_t batches_per_chain,
+              int64_t spacer, double alpha_ci, double alpha_ran, pbn_skart_result *out, void *stream);
+
+/* -------------------------------------------------------------- drivers */
+
+typedef struct pbn_two_state_query {
+    int64_t omega;           /* chains, >= 2 */
+    int64_t psi0;            /* initial G&R burn-in */
+    double rhat_threshold;   /* converged when R-hat < threshold */
+    double eps, r, s;        /* Alg. 1 parameters */
+    int64_t max_length;      /* cap on the chain length */
+    uint64_t seed;
+    int32_t perturb_mode;
+    pbn_soi soi;
+} pbn_two_state_query;
+
+typedef struct pbn_two_state_report {
+    double prob, rhat, alpha, beta;
+    int64_t psi, gr_psi, length, sample_size, M, N, ones;
+    int64_t n4[4];
+    int32_t gr_rounds, ts_rounds;
+    int64_t chain_node_updates;   /* omega * length * n */
+    double device_ms;             /* device time of the whole query */
+    double sim_ms;                /* CUDA-event time of the simulation launches (same stream) */
+    int64_t sim_launches;         /* simulation kernel launches */
+    int64_t kernel_launches;      /* all kernel launches of the query */
+    int64_t sim_items;            /* (node, chain group, transition) items simulated */
+    int64_t d2h_bytes;            /* device -> host bytes read for the stopping decisions */
+} pbn_two_state_report;
+
+/* Alg. GR then Alg. 3 (Sec. 4.2) end to end on the device: chains are
+ * extended, checked and extended again until the two-state rule and the
+ * burn-in check hold; only the stopping decisions cross to the host.
+ * Allocates its own device buffers.  Synchronises `stream`.
+ * Errors: PBN_ERR_NOT_CONVERGED (max_length), PBN_ERR_INVALID, PBN_ERR_OOM, PBN_ERR_CUDA. */
+int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_query *q, pbn_two_state_report *out,
+                           void *stream);
+
+typedef struct pbn_skart_query {
+    int64_t omega;
+    int64_t psi0;
+    double rhat_threshold;
+    double H_star;           /* precision requirement */
+    int32_t relative;        /* 1: the requirement is H_star * |mean| */
+    double alpha;            /* CI level 1 - alpha */
+    int64_t max_length;
+    uint64_t seed;
+    int32_t perturb_mode;
+    pbn_soi soi;
+} pbn_skart_query;
+
+typedef struct pbn_skart_report {
+    double mean, ci_lo, ci_hi, H, var, skew, phi, rhat;
+    int64_t psi, length, kappa, batches, spacer, sample_size;
+    int32_t gr_rounds, rand_rounds, ci_rounds;
+    int64_t chain_node_updates;
+    double device_ms;
+    double sim_ms;
+    int64_t sim_launches, kernel_launches, sim_items, d2h_bytes;
+} pbn_skart_report;
+
+/* Alg. GR then Alg. 4 (Sec. 4.3) end to end on the device.  Synchronises
+ * `stream`.  Errors as pbn_estimate_two_state. */
+int pbn_estimate_skart(const pbn_net *net, const pbn_skart_query *q, pbn_skart_report *out, void *stream);
+
+/* ---------------------------------------------------------------- errors */
+
+const char *pbn_last_error(void);
+const char *pbn_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBN_H */

@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
     """Compile oracle.c into oracle/liboracle.so (plain -O2, single thread)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-shared", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-shared", "-fPIC",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -101,6 +101,8 @@ def lib():
             L.orc_uniform.argtypes = [u64, i32, u64, i64]; L.orc_uniform.restype = ctypes.c_uint32
             L.orc_init_states.argtypes = [vp, u64, i64, vp]
             L.orc_simulate.argtypes = [vp, i32, u64, i64, u64, i64, vp, vp, vp, i32, vp, i64]
+            L.orc_simulate_from.argtypes = [vp, i32, u64, i64, i64, u64, i64, vp, vp, vp, i32, vp, i64]
+            L.orc_init_states_from.argtypes = [vp, u64, i64, i64, vp]
             L.orc_gelman_rubin.argtypes = [vp, i64, i64, i64, i64]; L.orc_gelman_rubin.restype = dbl
             L.orc_norm_ppf.argtypes = [dbl]; L.orc_norm_ppf.restype = dbl
             L.orc_t_ppf.argtypes = [dbl, dbl]; L.orc_t_ppf.restype = dbl
@@ -166,18 +168,20 @@ def uniform(seed: int, node: int, t: int, chain: int) -> int:
     return int(lib().orc_uniform(seed, node, t, chain))
 
 
-def init_states(net, seed: int, omega: int) -> np.ndarray:
+def init_states(net, seed: int, omega: int, chain0: int = 0) -> np.ndarray:
+    """Initial states of chains chain0 .. chain0+omega-1 as uint8 [omega, n]."""
     h = NetHandle(net)
     st = np.zeros((omega, net.n), dtype=np.uint8)
-    lib().orc_init_states(h.ref, seed, omega, _ptr(st))
+    lib().orc_init_states_from(h.ref, seed, chain0, omega, _ptr(st))
     return st
 
 
-def simulate(net, mode: int, seed: int, states: np.ndarray, t0: int, steps: int, soi=None, record=True):
-    """Advance states (uint8 [omega, n], modified copy returned) by `steps`
-    transitions starting at transition index t0.  Returns (states, ind) with
-    ind uint8 [omega, steps] (indicator of the state of interest after each
-    transition) or None."""
+def simulate(net, mode: int, seed: int, states: np.ndarray, t0: int, steps: int, soi=None, record=True,
+             chain0: int = 0):
+    """Advance states (uint8 [omega, n], modified copy returned) of chains
+    chain0 .. chain0+omega-1 by `steps` transitions starting at transition
+    index t0.  Returns (states, ind) with ind uint8 [omega, steps] (indicator
+    of the state of interest after each transition) or None."""
     h = NetHandle(net)
     st = np.ascontiguousarray(states, dtype=np.uint8).copy()
     omega = st.shape[0]
@@ -187,8 +191,8 @@ def simulate(net, mode: int, seed: int, states: np.ndarray, t0: int, steps: int,
         nodes = np.ascontiguousarray(soi.nodes, dtype=np.int32); vals = np.ascontiguousarray(soi.values, dtype=np.uint8)
         k = len(nodes)
     ind = np.zeros((omega, steps), dtype=np.uint8) if record else None
-    rc = lib().orc_simulate(h.ref, mode, seed, omega, t0, steps, _ptr(st), _ptr(nodes), _ptr(vals), k,
-                            _ptr(ind) if record else None, steps)
+    rc = lib().orc_simulate_from(h.ref, mode, seed, chain0, omega, t0, steps, _ptr(st), _ptr(nodes), _ptr(vals),
+                                 k, _ptr(ind) if record else None, steps)
     if rc:
         raise RuntimeError(f"orc_simulate failed: {rc}")
     return st, ind

@@ -165,16 +165,21 @@ uint32_t orc_uniform(uint64_t seed, int32_t node, uint64_t t, int64_t chain) {
 }
 
 /* Initial states (any initial state is allowed, Sec. 2.2; here fair coins). */
-void orc_init_states(const orc_net *net, uint64_t seed, int64_t omega, uint8_t *states) {
+void orc_init_states_from(const orc_net *net, uint64_t seed, int64_t chain0, int64_t omega, uint8_t *states) {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    for (int64_t c = 0; c < omega; c++) {
+    for (int64_t row = 0; row < omega; row++) {
+        int64_t c = chain0 + row;
         for (int i = 0; i < net->n; i++) {
             uint32_t ctr[4] = {(uint32_t)i, 0xFFFFFFFFu, 0xFFFFFFFFu, (uint32_t)((uint64_t)c >> 5)};
             uint32_t out[4];
             orc_philox4x32_10(ctr, key, out);
-            states[c * net->n + i] = (uint8_t)((out[0] >> (c & 31)) & 1u);
+            states[row * net->n + i] = (uint8_t)((out[0] >> (c & 31)) & 1u);
         }
     }
+}
+
+void orc_init_states(const orc_net *net, uint64_t seed, int64_t omega, uint8_t *states) {
+    orc_init_states_from(net, seed, 0, omega, states);
 }
 
 /* Category of u at node i (0 = perturbed, j+1 = function j). */
@@ -206,9 +211,9 @@ static int indicator(const uint8_t *s, const int32_t *soi_nodes, const uint8_t *
  * perturbations).  ind (may be NULL) receives ind[c*ind_stride + s] = indicator
  * of the meta state (Sec. 3.1) of chain c's state after transition t0+s.
  */
-int orc_simulate(const orc_net *net, int mode, uint64_t seed, int64_t omega, uint64_t t0, int64_t steps,
-                 uint8_t *states, const int32_t *soi_nodes, const uint8_t *soi_values, int32_t soi_size,
-                 uint8_t *ind, int64_t ind_stride) {
+int orc_simulate_from(const orc_net *net, int mode, uint64_t seed, int64_t chain0, int64_t omega, uint64_t t0,
+                      int64_t steps, uint8_t *states, const int32_t *soi_nodes, const uint8_t *soi_values,
+                      int32_t soi_size, uint8_t *ind, int64_t ind_stride) {
     int n = net->n;
     uint64_t *thr = (uint64_t *)malloc(sizeof(uint64_t) * net->F);
     uint8_t *next = (uint8_t *)malloc((size_t)n);
@@ -217,16 +222,20 @@ int orc_simulate(const orc_net *net, int mode, uint64_t seed, int64_t omega, uin
     if (!thr || !next || !cat || !R) { free(thr); free(next); free(cat); free(R); return ORC_ERR_OOM; }
     orc_select_thresholds(net, thr);
     uint32_t P32 = orc_perturb_threshold(net->p);
-    int64_t groups = (omega + 31) / 32;
     for (int64_t s = 0; s < steps; s++) {
         uint64_t t = t0 + (uint64_t)s;
-        for (int64_t g = 0; g < groups; g++) {
-            /* the group's digit words for every node at transition t */
-            for (int i = 0; i < n; i++) digit_words(seed, i, t, (uint64_t)g, R + 32 * (size_t)i);
-            for (int lane = 0; lane < 32; lane++) {
-                int64_t c = g * 32 + lane;
-                if (c >= omega) break;
-                uint8_t *st = states + c * n;
+        int64_t cached_group = -1;
+        for (int64_t row = 0; row < omega; row++) {
+            int64_t c = chain0 + row;            /* global chain index */
+            int64_t g = c >> 5;
+            int lane = (int)(c & 31);
+            if (g != cached_group) {
+                /* the group's digit words for every node at transition t */
+                for (int i = 0; i < n; i++) digit_words(seed, i, t, (uint64_t)g, R + 32 * (size_t)i);
+                cached_group = g;
+            }
+            {
+                uint8_t *st = states + row * n;
                 int any_perturbed = 0;
                 for (int i = 0; i < n; i++) {
                     uint32_t u = uniform_from_words(R + 32 * (size_t)i, lane);
@@ -243,12 +252,20 @@ int orc_simulate(const orc_net *net, int mode, uint64_t seed, int64_t omega, uin
                     }
                 }
                 memcpy(st, next, (size_t)n);
-                if (ind) ind[c * ind_stride + s] = (uint8_t)indicator(st, soi_nodes, soi_values, soi_size);
+                if (ind) ind[row * ind_stride + s] = (uint8_t)indicator(st, soi_nodes, soi_values, soi_size);
             }
         }
     }
     free(thr); free(next); free(cat); free(R);
     return ORC_OK;
+}
+
+/* Chains 0 .. omega-1 (see orc_simulate_from). */
+int orc_simulate(const orc_net *net, int mode, uint64_t seed, int64_t omega, uint64_t t0, int64_t steps,
+                 uint8_t *states, const int32_t *soi_nodes, const uint8_t *soi_values, int32_t soi_size,
+                 uint8_t *ind, int64_t ind_stride) {
+    return orc_simulate_from(net, mode, seed, 0, omega, t0, steps, states, soi_nodes, soi_values, soi_size, ind,
+                             ind_stride);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -1,0 +1,354 @@
+"""Python binding of libpbn_gb300.so, the C-ABI GB300 engine for parallel
+approximate steady-state analysis of probabilistic Boolean networks.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides device memory (tensors whose data pointers are
+passed through the ABI) and the current CUDA stream.  The binding fails loudly
+when the compiled library is missing; there is no CPU path.
+
+Entry points keep the C names (see include/pbn.h): pbn_load, pbn_init_chains,
+pbn_run_chains, pbn_gelman_rubin, pbn_two_state, pbn_skart,
+pbn_estimate_two_state, pbn_estimate_skart.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpbn_gb300.so")
+
+PBN_OK = 0
+PBN_ERR_INVALID = 1
+PBN_ERR_OOM = 2
+PBN_ERR_CUDA = 3
+PBN_ERR_TIMEOUT = 4
+PBN_ERR_NOT_CONVERGED = 5
+PBN_ERR_INSUFFICIENT = 6
+PBN_ERR_UNSUPPORTED = 7
+PER_NODE = 0
+GLOBAL = 1
+MAX_SOI = 32
+
+
+class PbnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"pbn status {status}: {msg}")
+        self.status = status
+
+
+# ----------------------------------------------------------- ABI structures
+
+c_i32, c_i64, c_u32, c_u64, c_dbl, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64,
+                                           ctypes.c_double, ctypes.c_void_p)
+
+
+class NetworkDesc(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("n_functions", c_i32), ("fn_offset", c_vp), ("par_offset", c_vp),
+                ("parents", c_vp), ("truth_table", c_vp), ("select_prob", c_vp), ("p", c_dbl)]
+
+
+class NetInfo(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("n_functions", c_i32), ("perturb_threshold", c_u32), ("table_bytes", c_i64)]
+
+
+class Soi(ctypes.Structure):
+    _fields_ = [("size", c_i32), ("nodes", c_vp), ("values", c_vp)]
+
+
+class Chains(ctypes.Structure):
+    _fields_ = [("omega", c_i64), ("state", c_vp), ("bits", c_vp), ("bits_cap", c_i64), ("bits_base", c_i64),
+                ("length", c_i64)]
+
+
+class RunCfg(ctypes.Structure):
+    _fields_ = [("seed", c_u64), ("perturb_mode", c_i32), ("soi", Soi), ("groups_per_block", c_i32),
+                ("threads_per_block", c_i32)]
+
+
+class GrResult(ctypes.Structure):
+    _fields_ = [("rhat", c_dbl), ("W", c_dbl), ("B", c_dbl), ("sigma2", c_dbl), ("S1", c_u64), ("S2_lo", c_u64),
+                ("S2_hi", c_u64)]
+
+
+class TwoStateResult(ctypes.Structure):
+    _fields_ = [("n00", c_i64), ("n01", c_i64), ("n10", c_i64), ("n11", c_i64), ("ones", c_i64),
+                ("alpha", c_dbl), ("beta", c_dbl), ("prob", c_dbl), ("M", c_i64), ("N", c_i64),
+                ("status", c_i32), ("pad", c_i32)]
+
+
+class SkartResult(ctypes.Structure):
+    _fields_ = [(k, c_dbl) for k in ("mean", "var", "skew", "phi", "A", "H", "ci_lo", "ci_hi", "vn_stat")] + \
+               [("vn_pass", c_i32), ("pad", c_i32), ("batches", c_i64)]
+
+
+class TwoStateQuery(ctypes.Structure):
+    _fields_ = [("omega", c_i64), ("psi0", c_i64), ("rhat_threshold", c_dbl), ("eps", c_dbl), ("r", c_dbl),
+                ("s", c_dbl), ("max_length", c_i64), ("seed", c_u64), ("perturb_mode", c_i32), ("soi", Soi)]
+
+
+class TwoStateReport(ctypes.Structure):
+    _fields_ = [("prob", c_dbl), ("rhat", c_dbl), ("alpha", c_dbl), ("beta", c_dbl), ("psi", c_i64),
+                ("gr_psi", c_i64), ("length", c_i64), ("sample_size", c_i64), ("M", c_i64), ("N", c_i64),
+                ("ones", c_i64), ("n4", c_i64 * 4), ("gr_rounds", c_i32), ("ts_rounds", c_i32),
+                ("chain_node_updates", c_i64), ("device_ms", c_dbl), ("sim_ms", c_dbl), ("sim_launches", c_i64),
+                ("kernel_launches", c_i64), ("sim_items", c_i64), ("d2h_bytes", c_i64)]
+
+
+class SkartQuery(ctypes.Structure):
+    _fields_ = [("omega", c_i64), ("psi0", c_i64), ("rhat_threshold", c_dbl), ("H_star", c_dbl),
+                ("relative", c_i32), ("alpha", c_dbl), ("max_length", c_i64), ("seed", c_u64),
+                ("perturb_mode", c_i32), ("soi", Soi)]
+
+
+class SkartReport(ctypes.Structure):
+    _fields_ = [(k, c_dbl) for k in ("mean", "ci_lo", "ci_hi", "H", "var", "skew", "phi", "rhat")] + \
+               [(k, c_i64) for k in ("psi", "length", "kappa", "batches", "spacer", "sample_size")] + \
+               [("gr_rounds", c_i32), ("rand_rounds", c_i32), ("ci_rounds", c_i32),
+                ("chain_node_updates", c_i64), ("device_ms", c_dbl), ("sim_ms", c_dbl), ("sim_launches", c_i64),
+                ("kernel_launches", c_i64), ("sim_items", c_i64), ("d2h_bytes", c_i64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded C-ABI library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                                  "(the CUDA extension is required; there is no CPU path)")
+            L = ctypes.CDLL(LIB_PATH)
+            P = ctypes.POINTER
+            L.pbn_load.argtypes = [P(NetworkDesc), P(c_vp)]
+            L.pbn_free.argtypes = [c_vp]
+            L.pbn_free.restype = None
+            L.pbn_net_get_info.argtypes = [c_vp, P(NetInfo)]
+            L.pbn_init_chains.argtypes = [c_vp, P(RunCfg), P(Chains), c_vp]
+            L.pbn_run_chains.argtypes = [c_vp, P(RunCfg), P(Chains), c_i64, c_vp]
+            L.pbn_gelman_rubin.argtypes = [P(Chains), c_i64, c_i64, c_vp, c_vp]
+            L.pbn_two_state.argtypes = [P(Chains), c_i64, c_i64, c_dbl, c_dbl, c_dbl, c_vp, c_vp]
+            L.pbn_skart.argtypes = [P(Chains), c_i64, c_i64, c_i64, c_i64, c_dbl, c_dbl, c_vp, c_vp]
+            L.pbn_estimate_two_state.argtypes = [c_vp, P(TwoStateQuery), P(TwoStateReport), c_vp]
+            L.pbn_estimate_skart.argtypes = [c_vp, P(SkartQuery), P(SkartReport), c_vp]
+            L.pbn_last_error.restype = ctypes.c_char_p
+            L.pbn_status_string.restype = ctypes.c_char_p
+            L.pbn_status_string.argtypes = [ctypes.c_int]
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != PBN_OK:
+        raise PbnError(rc, lib().pbn_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_vp(s.cuda_stream)
+
+
+def _as_struct(cls, obj):
+    return {k: (list(getattr(obj, k)) if k == "n4" else getattr(obj, k)) for k, _ in cls._fields_ if k != "pad"}
+
+
+# ------------------------------------------------------------------ network
+
+class Network:
+    """A PBN staged on the device (owns the pbn_net handle)."""
+
+    def __init__(self, net):
+        self._arrays = dict(
+            fn_offset=np.ascontiguousarray(net.fn_offset, dtype=np.int32),
+            par_offset=np.ascontiguousarray(net.par_offset, dtype=np.int32),
+            parents=np.ascontiguousarray(net.parents if len(net.parents) else np.zeros(1, np.int32), dtype=np.int32),
+            truth_table=np.ascontiguousarray(net.truth_table, dtype=np.uint32),
+            select_prob=np.ascontiguousarray(net.select_prob, dtype=np.float64))
+        a = self._arrays
+        desc = NetworkDesc(int(net.n), int(a["fn_offset"][-1]), a["fn_offset"].ctypes.data, a["par_offset"].ctypes.data,
+                           a["parents"].ctypes.data, a["truth_table"].ctypes.data, a["select_prob"].ctypes.data,
+                           float(net.p))
+        h = c_vp()
+        _check(lib().pbn_load(ctypes.byref(desc), ctypes.byref(h)))
+        self.handle = h
+        self.n = int(net.n)
+        self.n_functions = int(a["fn_offset"][-1])
+
+    def info(self) -> dict:
+        o = NetInfo()
+        _check(lib().pbn_net_get_info(self.handle, ctypes.byref(o)))
+        return _as_struct(NetInfo, o)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pbn_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pbn_load(net) -> Network:
+    return Network(net)
+
+
+def pbn_load_pinned(host_arrays: dict, n: int, p: float) -> Network:
+    """Stage a network whose CSR arrays are pinned host tensors (keys
+    fn_offset, par_offset, parents, truth_table, select_prob): pbn_load then
+    copies them to the device from page-locked memory."""
+    self = Network.__new__(Network)
+    self._arrays = host_arrays
+    a = host_arrays
+    desc = NetworkDesc(int(n), int(a["fn_offset"][-1]), a["fn_offset"].data_ptr(), a["par_offset"].data_ptr(),
+                       a["parents"].data_ptr(), a["truth_table"].data_ptr(), a["select_prob"].data_ptr(), float(p))
+    h = c_vp()
+    _check(lib().pbn_load(ctypes.byref(desc), ctypes.byref(h)))
+    self.handle = h
+    self.n = int(n)
+    self.n_functions = int(a["fn_offset"][-1])
+    return self
+
+
+class SoiArg:
+    def __init__(self, soi):
+        if soi is None:
+            self.nodes = np.zeros(1, np.int32); self.values = np.zeros(1, np.uint8); self.size = 0
+        else:
+            self.nodes = np.ascontiguousarray(soi.nodes, dtype=np.int32)
+            self.values = np.ascontiguousarray(soi.values, dtype=np.uint8)
+            self.size = len(self.nodes)
+        self.struct = Soi(self.size, self.nodes.ctypes.data, self.values.ctypes.data)
+
+
+# ------------------------------------------------------------------- chains
+
+class ChainSet:
+    """omega chains of one network in caller-owned device memory (torch
+    tensors): bit-sliced states [G, n] and an indicator bitstream [G, cap]."""
+
+    def __init__(self, network: Network, omega: int, bits_cap: int = 0, bits_base: int = 0):
+        torch = _torch()
+        self.network = network
+        self.omega = int(omega)
+        self.G = (self.omega + 31) // 32
+        self.state = torch.zeros((self.G, network.n), dtype=torch.int32, device="cuda")
+        self.bits = torch.zeros((self.G, max(bits_cap, 1)), dtype=torch.int32, device="cuda") if bits_cap else None
+        self.c = Chains(self.omega, self.state.data_ptr(), self.bits.data_ptr() if self.bits is not None else None,
+                        int(bits_cap), int(bits_base), 0)
+
+    @property
+    def length(self) -> int:
+        return int(self.c.length)
+
+    def states_numpy(self) -> np.ndarray:
+        """Node values as uint8 [omega, n] (unpacked from the bit-sliced words)."""
+        w = self.state.cpu().numpy().view(np.uint32)
+        lanes = np.arange(32, dtype=np.uint32)
+        bits = ((w[:, None, :] >> lanes[None, :, None]) & 1).astype(np.uint8)  # [G, 32, n]
+        return bits.reshape(self.G * 32, -1)[: self.omega]
+
+    def set_states(self, states: np.ndarray):
+        """Pack uint8 [omega, n] node values into the bit-sliced layout."""
+        torch = _torch()
+        st = np.zeros((self.G * 32, self.network.n), dtype=np.uint64)
+        st[: self.omega] = states
+        st = st.reshape(self.G, 32, -1)
+        w = (st << np.arange(32, dtype=np.uint64)[None, :, None]).sum(axis=1).astype(np.uint32)
+        self.state.copy_(torch.from_numpy(w.view(np.int32)))
+
+    def indicator_numpy(self, start: int, length: int) -> np.ndarray:
+        """Indicator bits uint8 [omega, length] of positions start .. start+length-1."""
+        col = start - int(self.c.bits_base)
+        w = self.bits[:, col:col + length].cpu().numpy().view(np.uint32)
+        lanes = np.arange(32, dtype=np.uint32)
+        b = ((w[:, None, :] >> lanes[None, :, None]) & 1).astype(np.uint8)  # [G, 32, len]
+        return b.reshape(self.G * 32, length)[: self.omega]
+
+
+def _cfg(seed, mode, soi_arg, groups_per_block=0, threads_per_block=0):
+    return RunCfg(int(seed), int(mode), soi_arg.struct, int(groups_per_block), int(threads_per_block))
+
+
+def pbn_init_chains(chains: ChainSet, seed: int, mode: int = PER_NODE, stream=None):
+    soi = SoiArg(None)
+    cfg = _cfg(seed, mode, soi)
+    _check(lib().pbn_init_chains(chains.network.handle, ctypes.byref(cfg), ctypes.byref(chains.c), _stream(stream)))
+
+
+def pbn_run_chains(chains: ChainSet, steps: int, seed: int, mode: int = PER_NODE, soi=None,
+                   groups_per_block: int = 0, threads_per_block: int = 0, stream=None):
+    soi_arg = SoiArg(soi)
+    cfg = _cfg(seed, mode, soi_arg, groups_per_block, threads_per_block)
+    _check(lib().pbn_run_chains(chains.network.handle, ctypes.byref(cfg), ctypes.byref(chains.c), int(steps),
+                                _stream(stream)))
+
+
+def _device_result(cls, call):
+    torch = _torch()
+    buf = torch.zeros(ctypes.sizeof(cls), dtype=torch.uint8, device="cuda")
+    call(c_vp(buf.data_ptr()))
+    host = buf.cpu().numpy().tobytes()
+    return cls.from_buffer_copy(host)
+
+
+def pbn_gelman_rubin(chains: ChainSet, start: int, psi: int, stream=None) -> dict:
+    r = _device_result(GrResult, lambda p: _check(lib().pbn_gelman_rubin(
+        ctypes.byref(chains.c), int(start), int(psi), p, _stream(stream))))
+    out = _as_struct(GrResult, r)
+    out["S2"] = (r.S2_hi << 64) | r.S2_lo
+    return out
+
+
+def pbn_two_state(chains: ChainSet, start: int, length: int, eps: float, r: float, s: float, stream=None) -> dict:
+    res = _device_result(TwoStateResult, lambda p: _check(lib().pbn_two_state(
+        ctypes.byref(chains.c), int(start), int(length), float(eps), float(r), float(s), p, _stream(stream))))
+    return _as_struct(TwoStateResult, res)
+
+
+def pbn_skart(chains: ChainSet, start: int, kappa: int, batches_per_chain: int, spacer: int, alpha_ci: float,
+              alpha_ran: float = 0.20, stream=None) -> dict:
+    res = _device_result(SkartResult, lambda p: _check(lib().pbn_skart(
+        ctypes.byref(chains.c), int(start), int(kappa), int(batches_per_chain), int(spacer), float(alpha_ci),
+        float(alpha_ran), p, _stream(stream))))
+    return _as_struct(SkartResult, res)
+
+
+def pbn_estimate_two_state(network: Network, soi, omega: int, seed: int, psi0: int = 1024, rhat: float = 1.05,
+                           eps: float = 1e-10, r: float = 0.005, s: float = 0.95, mode: int = PER_NODE,
+                           max_length: int = 1 << 26, stream=None) -> dict:
+    """Alg. GR then Alg. 3 end to end; returns the report as a dict."""
+    soi_arg = SoiArg(soi)
+    q = TwoStateQuery(int(omega), int(psi0), float(rhat), float(eps), float(r), float(s), int(max_length), int(seed),
+                      int(mode), soi_arg.struct)
+    out = TwoStateReport()
+    _check(lib().pbn_estimate_two_state(network.handle, ctypes.byref(q), ctypes.byref(out), _stream(stream)))
+    return _as_struct(TwoStateReport, out)
+
+
+def pbn_estimate_skart(network: Network, soi, omega: int, seed: int, H_star: float, relative: bool = True,
+                       alpha: float = 0.05, psi0: int = 1024, rhat: float = 1.05, mode: int = PER_NODE,
+                       max_length: int = 1 << 26, stream=None) -> dict:
+    """Alg. GR then Alg. 4 end to end; returns the report as a dict."""
+    soi_arg = SoiArg(soi)
+    q = SkartQuery(int(omega), int(psi0), float(rhat), float(H_star), int(bool(relative)), float(alpha),
+                   int(max_length), int(seed), int(mode), soi_arg.struct)
+    out = SkartReport()
+    _check(lib().pbn_estimate_skart(network.handle, ctypes.byref(q), ctypes.byref(out), _stream(stream)))
+    return _as_struct(SkartReport, out)

@@ -1,0 +1,682 @@
+// C ABI of the GB300 PBN engine: network staging, chain runs, statistics and
+// the end-to-end drivers (Alg. GR followed by Alg. 3 or Alg. 4).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pbn_internal.cuh"
+
+struct pbn_net {
+  pbn::NetDev dev;
+  int device = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? PBN_ERR_OOM : PBN_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr, what)                      \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) return cuda_fail(_e, what); \
+  } while (0)
+
+// Quantisation of the perturbation probability: P32 = round(p 2^32), at most 2^32-1.
+uint32_t quantise_p(double p) {
+  long long q = llround(p * 4294967296.0);
+  if (q < 0) q = 0;
+  if (q > 4294967295LL) q = 4294967295LL;
+  return (uint32_t)q;
+}
+
+int sm_count() {
+  static int v = 0;
+  if (!v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+  }
+  return v;
+}
+
+// Scratch of the primitive statistics entry points, one per stream.
+std::mutex g_scratch_mu;
+std::map<std::pair<int, cudaStream_t>, pbn::StatsScratch> g_scratch;
+
+int scratch_for(cudaStream_t s, pbn::StatsScratch **out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  auto key = std::make_pair(dev, s);
+  auto it = g_scratch.find(key);
+  if (it == g_scratch.end()) {
+    pbn::StatsScratch sc;
+    cudaError_t e = pbn::scratch_init(sc, s);
+    if (e != cudaSuccess) {
+      pbn::scratch_free(sc);
+      return cuda_fail(e, "statistics scratch");
+    }
+    it = g_scratch.emplace(key, sc).first;
+  }
+  *out = &it->second;
+  return PBN_OK;
+}
+
+int check_soi(const pbn_soi &soi, int n, bool allow_empty) {
+  if (soi.size == 0 && allow_empty) return PBN_OK;
+  if (soi.size < 1 || soi.size > PBN_MAX_SOI) return fail(PBN_ERR_INVALID, "state of interest size %d", soi.size);
+  if (!soi.nodes || !soi.values) return fail(PBN_ERR_INVALID, "state of interest arrays are NULL");
+  for (int m = 0; m < soi.size; m++) {
+    if (soi.nodes[m] < 0 || soi.nodes[m] >= n) return fail(PBN_ERR_INVALID, "SOI node %d out of range", soi.nodes[m]);
+    if (soi.values[m] > 1) return fail(PBN_ERR_INVALID, "SOI value must be 0 or 1");
+  }
+  return PBN_OK;
+}
+
+struct LaunchPlan {
+  int gpb, threads;
+  size_t smem;
+  bool tables_in_smem;
+};
+
+int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, int threads_req, LaunchPlan *p) {
+  const int G = (int)((omega + 31) / 32);
+  const int maxs = pbn::sim_max_smem();
+  int gpb = gpb_req > 0 ? gpb_req : std::max(1, (G + sm_count() - 1) / sm_count());
+  gpb = std::min(gpb, std::max(G, 1));
+  for (;;) {
+    size_t with = pbn::sim_smem_bytes(net.n, net.F, gpb, mode, true);
+    size_t without = pbn::sim_smem_bytes(net.n, net.F, gpb, mode, false);
+    if ((int64_t)with <= maxs) { p->tables_in_smem = true; p->smem = with; break; }
+    if ((int64_t)without <= maxs) { p->tables_in_smem = false; p->smem = without; break; }
+    if (gpb == 1) return fail(PBN_ERR_UNSUPPORTED, "chain state of one group does not fit shared memory");
+    gpb = std::max(1, gpb / 2);
+  }
+  int items = net.n * gpb;
+  int threads = threads_req > 0 ? threads_req : std::min(1024, std::max(32, (items + 31) / 32 * 32));
+  if (threads % 32 || threads > 1024) return fail(PBN_ERR_INVALID, "threads_per_block %d", threads);
+  p->gpb = gpb;
+  p->threads = threads;
+  return PBN_OK;
+}
+
+pbn::SimArgs make_args(const pbn::NetDev &net, const pbn_run_cfg &cfg, const pbn_chains &ch, int64_t steps,
+                       const LaunchPlan &plan) {
+  pbn::SimArgs a;
+  memset(&a, 0, sizeof a);
+  a.rk = pbn::make_round_keys(cfg.seed);
+  a.node = net.d_node;
+  a.fn = net.d_fn;
+  a.state = ch.state;
+  a.bits = ch.bits;
+  a.bits_cap = ch.bits_cap;
+  a.col0 = ch.length - ch.bits_base;
+  a.omega = ch.omega;
+  a.t0 = (uint64_t)ch.length;
+  a.n = net.n;
+  a.F = net.F;
+  a.G = (int)((ch.omega + 31) / 32);
+  a.steps = (int)steps;
+  a.gpb = plan.gpb;
+  a.P32 = net.P32;
+  a.tables_in_smem = plan.tables_in_smem ? 1 : 0;
+  a.soi_size = (ch.bits && ch.bits_cap > 0) ? cfg.soi.size : 0;
+  a.soi_val = 0;
+  for (int m = 0; m < cfg.soi.size && m < PBN_MAX_SOI; m++) {
+    a.soi_node[m] = (uint16_t)cfg.soi.nodes[m];
+    if (cfg.soi.values[m]) a.soi_val |= 1u << m;
+  }
+  return a;
+}
+
+int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, cudaStream_t s) {
+  if (steps < 0) return fail(PBN_ERR_INVALID, "negative step count");
+  if (steps == 0) return PBN_OK;
+  const bool record = ch.bits && ch.bits_cap > 0 && cfg.soi.size > 0;
+  if (record) {
+    const int64_t last = ch.length + steps - 1 - ch.bits_base;
+    if (last >= ch.bits_cap) return fail(PBN_ERR_INVALID, "bitstream capacity %lld too small for position %lld",
+                                         (long long)ch.bits_cap, (long long)(ch.length + steps - 1));
+  }
+  LaunchPlan plan;
+  int rc = plan_launch(net, ch.omega, cfg.perturb_mode, cfg.groups_per_block, cfg.threads_per_block, &plan);
+  if (rc) return rc;
+  // one launch covers at most 2^30 steps; the step counter itself is 64-bit
+  const int64_t chunk = 1 << 30;
+  for (int64_t done = 0; done < steps; done += chunk) {
+    const int64_t k = std::min(chunk, steps - done);
+    pbn::SimArgs a = make_args(net, cfg, ch, k, plan);
+    if (!record) a.soi_size = 0;
+    CUDA_TRY(pbn::launch_sim(a, cfg.perturb_mode, plan.threads, plan.smem, s), "simulation launch");
+    ch.length += k;
+  }
+  return PBN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pbn_last_error(void) { return g_err.c_str(); }
+
+const char *pbn_status_string(int status) {
+  switch (status) {
+    case PBN_OK: return "ok";
+    case PBN_ERR_INVALID: return "invalid argument";
+    case PBN_ERR_OOM: return "out of memory";
+    case PBN_ERR_CUDA: return "CUDA error";
+    case PBN_ERR_TIMEOUT: return "device wait timed out";
+    case PBN_ERR_NOT_CONVERGED: return "not converged within the length cap";
+    case PBN_ERR_INSUFFICIENT: return "window cannot give alpha and beta";
+    case PBN_ERR_UNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+int pbn_load(const pbn_network_desc *d, pbn_net **out) {
+  if (!d || !out) return fail(PBN_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  const int n = d->n;
+  if (n < 1) return fail(PBN_ERR_INVALID, "n = %d", n);
+  if (n > PBN_MAX_NODES) return fail(PBN_ERR_UNSUPPORTED, "n = %d exceeds %d", n, PBN_MAX_NODES);
+  if (!d->fn_offset || !d->par_offset || !d->truth_table || !d->select_prob)
+    return fail(PBN_ERR_INVALID, "NULL network array");
+  if (!(d->p >= 0.0 && d->p < 1.0)) return fail(PBN_ERR_INVALID, "perturbation probability %g", d->p);
+  const int F = d->n_functions;
+  if (d->fn_offset[0] != 0 || d->fn_offset[n] != F) return fail(PBN_ERR_INVALID, "fn_offset does not span F");
+  if (F > 65535) return fail(PBN_ERR_UNSUPPORTED, "F = %d exceeds 65535", F);
+  if (d->par_offset[0] != 0) return fail(PBN_ERR_INVALID, "par_offset[0] != 0");
+  const uint32_t P32 = quantise_p(d->p);
+  const uint64_t span = 4294967296ull - P32;
+  std::vector<uint4> fn(F);
+  std::vector<uint32_t> node(n);
+  std::vector<std::pair<uint64_t, int>> order(n);
+  int max_l = 0;
+  for (int i = 0; i < n; i++) {
+    const int f0 = d->fn_offset[i], f1 = d->fn_offset[i + 1];
+    const int l = f1 - f0;
+    if (l < 1) return fail(PBN_ERR_INVALID, "node %d has no predictor function", i);
+    if (l > PBN_MAX_FUNCTIONS_PER_NODE)
+      return fail(PBN_ERR_UNSUPPORTED, "node %d has %d functions (max %d)", i, l, PBN_MAX_FUNCTIONS_PER_NODE);
+    max_l = std::max(max_l, l);
+    double sum = 0.0, S = 0.0;
+    uint64_t shape = (uint64_t)l;
+    for (int f = f0; f < f1; f++) {
+      const double c = d->select_prob[f];
+      if (!(c >= 0.0 && c <= 1.0)) return fail(PBN_ERR_INVALID, "selection probability %g", c);
+      sum += c;
+      const int k = d->par_offset[f + 1] - d->par_offset[f];
+      if (k < 0) return fail(PBN_ERR_INVALID, "par_offset decreasing at %d", f);
+      if (k > PBN_MAX_PARENTS) return fail(PBN_ERR_UNSUPPORTED, "function %d has %d parents", f, k);
+      shape = shape * 8 + (uint64_t)k;
+      int par[5] = {0, 0, 0, 0, 0};
+      for (int m = 0; m < k; m++) {
+        const int v = d->parents[d->par_offset[f] + m];
+        if (v < 0 || v >= n) return fail(PBN_ERR_INVALID, "parent %d out of range", v);
+        par[m] = v;
+      }
+      // upper category bound of function f (the last one of a node is 2^32, never compared)
+      uint32_t T = 0xFFFFFFFFu;
+      S += c;
+      if (f < f1 - 1) {
+        long long q = llround((double)span * S);
+        if (q < 0) q = 0;
+        if ((uint64_t)q > span) q = (long long)span;
+        uint64_t t = (uint64_t)P32 + (uint64_t)q;
+        T = t > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)t;
+      }
+      uint4 r;
+      r.x = d->truth_table[f];
+      r.y = T;
+      r.z = (uint32_t)par[0] | ((uint32_t)par[1] << 12) | (((uint32_t)par[4] & 0xFFu) << 24);
+      r.w = (uint32_t)par[2] | ((uint32_t)par[3] << 12) | (((uint32_t)par[4] >> 8) << 24) | ((uint32_t)k << 28);
+      fn[f] = r;
+    }
+    if (fabs(sum - 1.0) > 1e-9) return fail(PBN_ERR_INVALID, "selection probabilities of node %d sum to %.17g", i, sum);
+    node[i] = (uint32_t)i | ((uint32_t)(l - 1) << 12) | ((uint32_t)f0 << 16);
+    order[i] = std::make_pair(shape, i);
+  }
+  // processing order: nodes of the same shape (l, k of each function) next to
+  // each other so a warp's threads take the same branches; the synchronous
+  // update makes the order immaterial to the result.
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<uint64_t, int> &a, const std::pair<uint64_t, int> &b) { return a.first < b.first; });
+  std::vector<uint32_t> node_sorted(n);
+  for (int r = 0; r < n; r++) node_sorted[r] = node[order[r].second];
+  pbn_net *net = new pbn_net();
+  cudaGetDevice(&net->device);
+  net->dev.n = n;
+  net->dev.F = F;
+  net->dev.P32 = P32;
+  net->dev.max_l = max_l;
+  cudaError_t e = cudaMalloc(&net->dev.d_fn, sizeof(uint4) * (size_t)F);
+  if (e == cudaSuccess) e = cudaMalloc(&net->dev.d_node, sizeof(uint32_t) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMemcpy(net->dev.d_fn, fn.data(), sizeof(uint4) * (size_t)F, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(net->dev.d_node, node_sorted.data(), sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    pbn_free(net);
+    return cuda_fail(e, "staging network tables");
+  }
+  net->dev.table_bytes = (int64_t)F * 16 + (int64_t)n * 4;
+  *out = net;
+  return PBN_OK;
+}
+
+void pbn_free(pbn_net *net) {
+  if (!net) return;
+  if (net->dev.d_fn) cudaFree(net->dev.d_fn);
+  if (net->dev.d_node) cudaFree(net->dev.d_node);
+  delete net;
+}
+
+int pbn_net_get_info(const pbn_net *net, pbn_net_info *out) {
+  if (!net || !out) return fail(PBN_ERR_INVALID, "NULL argument");
+  out->n = net->dev.n;
+  out->n_functions = net->dev.F;
+  out->perturb_threshold = net->dev.P32;
+  out->table_bytes = net->dev.table_bytes;
+  return PBN_OK;
+}
+
+int pbn_init_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *ch, void *stream) {
+  if (!net || !cfg || !ch) return fail(PBN_ERR_INVALID, "NULL argument");
+  if (ch->omega < 1 || !ch->state) return fail(PBN_ERR_INVALID, "chains: omega %lld, state %p", (long long)ch->omega, (void *)ch->state);
+  CUDA_TRY(pbn::launch_init(net->dev, cfg->seed, ch->state, ch->omega, (cudaStream_t)stream), "init launch");
+  ch->length = 0;
+  return PBN_OK;
+}
+
+int pbn_run_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *ch, int64_t steps, void *stream) {
+  if (!net || !cfg || !ch) return fail(PBN_ERR_INVALID, "NULL argument");
+  if (ch->omega < 1 || !ch->state) return fail(PBN_ERR_INVALID, "chains not initialised");
+  if (cfg->perturb_mode != PBN_PERTURB_PER_NODE && cfg->perturb_mode != PBN_PERTURB_GLOBAL)
+    return fail(PBN_ERR_INVALID, "perturb_mode %d", cfg->perturb_mode);
+  int rc = check_soi(cfg->soi, net->dev.n, true);
+  if (rc) return rc;
+  return run_steps(net->dev, *cfg, *ch, steps, (cudaStream_t)stream);
+}
+
+static int check_window(const pbn_chains *ch, int64_t start, int64_t len) {
+  if (!ch || !ch->bits) return fail(PBN_ERR_INVALID, "chains without bitstream");
+  if (len < 1 || start < ch->bits_base || start + len - ch->bits_base > ch->bits_cap || start + len > ch->length)
+    return fail(PBN_ERR_INVALID, "window [%lld, %lld) outside the recorded positions", (long long)start,
+                (long long)(start + len));
+  return PBN_OK;
+}
+
+int pbn_gelman_rubin(const pbn_chains *ch, int64_t start, int64_t psi, pbn_gr_result *out, void *stream) {
+  int rc = check_window(ch, start, psi);
+  if (rc) return rc;
+  if (ch->omega < 2 || psi < 2) return fail(PBN_ERR_INVALID, "Gelman-Rubin needs omega >= 2 and psi >= 2");
+  pbn::StatsScratch *sc;
+  if ((rc = scratch_for((cudaStream_t)stream, &sc))) return rc;
+  CUDA_TRY(pbn::launch_gelman_rubin(*ch, start - ch->bits_base, psi, out, *sc, (cudaStream_t)stream), "G&R launch");
+  return PBN_OK;
+}
+
+int pbn_two_state(const pbn_chains *ch, int64_t start, int64_t len, double eps, double r, double s,
+                  pbn_two_state_result *out, void *stream) {
+  int rc = check_window(ch, start, len);
+  if (rc) return rc;
+  if (!(eps > 0 && r > 0 && s > 0 && s < 1)) return fail(PBN_ERR_INVALID, "eps, r, s out of range");
+  pbn::StatsScratch *sc;
+  if ((rc = scratch_for((cudaStream_t)stream, &sc))) return rc;
+  CUDA_TRY(pbn::launch_two_state(*ch, start - ch->bits_base, len, eps, r, s, out, *sc, (cudaStream_t)stream),
+           "two-state launch");
+  return PBN_OK;
+}
+
+int pbn_skart(const pbn_chains *ch, int64_t start, int64_t kappa, int64_t bpc, int64_t spacer, double alpha_ci,
+              double alpha_ran, pbn_skart_result *out, void *stream) {
+  if (kappa < 1 || bpc < 1 || spacer < 0) return fail(PBN_ERR_INVALID, "kappa, batches, spacer");
+  if (kappa > (1ll << 30)) return fail(PBN_ERR_UNSUPPORTED, "batch size above 2^30");
+  int rc = check_window(ch, start, kappa * bpc);
+  if (rc) return rc;
+  if (ch->omega * bpc < 2) return fail(PBN_ERR_INVALID, "Skart needs at least 2 batches");
+  pbn::StatsScratch *sc;
+  if ((rc = scratch_for((cudaStream_t)stream, &sc))) return rc;
+  CUDA_TRY(pbn::launch_skart(*ch, start - ch->bits_base, kappa, bpc, spacer, alpha_ci, alpha_ran, out, *sc,
+                             (cudaStream_t)stream),
+           "Skart launch");
+  return PBN_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ drivers
+
+namespace {
+
+// Chains owned by one driver call: state, a growing bitstream window and the
+// statistics scratch, all stream-ordered allocations.
+struct Query {
+  const pbn::NetDev &net;
+  pbn_run_cfg cfg;
+  cudaStream_t s;
+  pbn_chains ch;
+  pbn::StatsScratch sc;
+  void *d_res = nullptr;   // device result slot
+  void *h_res = nullptr;   // pinned host copy
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> sim_ev;   // start/stop pairs around simulation launches
+  int64_t sim_launches = 0, kernel_launches = 0, sim_items = 0, d2h_bytes = 0;
+
+  Query(const pbn::NetDev &n, cudaStream_t st) : net(n), s(st) {
+    memset(&cfg, 0, sizeof cfg);
+    memset(&ch, 0, sizeof ch);
+  }
+  ~Query() {
+    if (ch.state) cudaFreeAsync(ch.state, s);
+    if (ch.bits) cudaFreeAsync(ch.bits, s);
+    if (d_res) cudaFreeAsync(d_res, s);
+    cudaStreamSynchronize(s);
+    pbn::scratch_free(sc);
+    if (h_res) cudaFreeHost(h_res);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (cudaEvent_t e : sim_ev) cudaEventDestroy(e);
+  }
+
+  int open(int64_t omega) {
+    ch.omega = omega;
+    const int G = (int)((omega + 31) / 32);
+    CUDA_TRY(cudaMallocAsync(&ch.state, sizeof(uint32_t) * (size_t)G * net.n, s), "state alloc");
+    CUDA_TRY(cudaMallocAsync(&d_res, 256, s), "result alloc");
+    CUDA_TRY(cudaMallocHost(&h_res, 256), "pinned alloc");
+    CUDA_TRY(pbn::scratch_init(sc, s), "scratch");
+    CUDA_TRY(cudaEventCreate(&ev0), "event");
+    CUDA_TRY(cudaEventCreate(&ev1), "event");
+    CUDA_TRY(cudaEventRecord(ev0, s), "event");
+    CUDA_TRY(pbn::launch_init(net, cfg.seed, ch.state, omega, s), "init");
+    kernel_launches++;
+    ch.length = 0;
+    return PBN_OK;
+  }
+
+  // Make the bitstream hold positions [base, upto): re-bases when nothing
+  // before `base` is needed any more, grows (copying the kept columns) otherwise.
+  int reserve(int64_t base, int64_t upto) {
+    const int G = (int)((ch.omega + 31) / 32);
+    if (ch.bits && base >= ch.bits_base && upto - ch.bits_base <= ch.bits_cap) return PBN_OK;
+    const int64_t keep_from = std::max(base, ch.bits_base);
+    const int64_t kept = ch.bits ? std::max<int64_t>(0, std::min(ch.length, ch.bits_base + ch.bits_cap) - keep_from) : 0;
+    int64_t cap = std::max<int64_t>(upto - base, 64);
+    cap = std::max<int64_t>(cap, 2 * (ch.bits ? (ch.length - base) : 0));
+    cap = (cap + 3) & ~int64_t(3);
+    uint32_t *nb = nullptr;
+    CUDA_TRY(cudaMallocAsync(&nb, sizeof(uint32_t) * (size_t)G * cap, s), "bitstream alloc");
+    if (ch.bits && kept > 0 && keep_from >= ch.bits_base) {
+      CUDA_TRY(cudaMemcpy2DAsync(nb + (keep_from - base), cap * 4, ch.bits + (keep_from - ch.bits_base), ch.bits_cap * 4,
+                                 kept * 4, G, cudaMemcpyDeviceToDevice, s),
+               "bitstream copy");
+    }
+    if (ch.bits) cudaFreeAsync(ch.bits, s);
+    ch.bits = nb;
+    ch.bits_cap = cap;
+    ch.bits_base = base;
+    return PBN_OK;
+  }
+
+  int extend_to(int64_t len, int64_t keep_from) {
+    if (len <= ch.length) return PBN_OK;
+    int rc = reserve(keep_from, len);
+    if (rc) return rc;
+    const int64_t steps = len - ch.length;
+    cudaEvent_t a, b;
+    CUDA_TRY(cudaEventCreate(&a), "event");
+    CUDA_TRY(cudaEventCreate(&b), "event");
+    sim_ev.push_back(a);
+    sim_ev.push_back(b);
+    CUDA_TRY(cudaEventRecord(a, s), "event");
+    rc = run_steps(net, cfg, ch, steps, s);
+    if (rc) return rc;
+    CUDA_TRY(cudaEventRecord(b, s), "event");
+    const int64_t launches = (steps + (1ll << 30) - 1) >> 30;
+    sim_launches += launches;
+    kernel_launches += launches;
+    sim_items += steps * (int64_t)net.n * ((ch.omega + 31) / 32);
+    return PBN_OK;
+  }
+
+  int stat_launched(int k) {
+    kernel_launches += k;
+    return PBN_OK;
+  }
+
+  template <typename T>
+  int fetch(T *h) {
+    CUDA_TRY(cudaMemcpyAsync(h_res, d_res, sizeof(T), cudaMemcpyDeviceToHost, s), "result copy");
+    CUDA_TRY(cudaStreamSynchronize(s), "stream sync");
+    memcpy(h, h_res, sizeof(T));
+    d2h_bytes += sizeof(T);
+    return PBN_OK;
+  }
+
+  double sim_ms() {
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < sim_ev.size(); k += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, sim_ev[k], sim_ev[k + 1]) == cudaSuccess) total += ms;
+    }
+    return total;
+  }
+
+  int gelman_rubin(int64_t psi0, double thr, int64_t max_length, int64_t *psi_out, double *rhat, int32_t *rounds) {
+    int64_t psi = psi0;
+    *rounds = 0;
+    for (;;) {
+      if (2 * psi > max_length) return fail(PBN_ERR_NOT_CONVERGED, "Gelman-Rubin not converged below length %lld", (long long)max_length);
+      int rc = extend_to(2 * psi, psi);
+      if (rc) return rc;
+      CUDA_TRY(pbn::launch_gelman_rubin(ch, psi - ch.bits_base, psi, (pbn_gr_result *)d_res, sc, s), "G&R");
+      stat_launched(1);
+      pbn_gr_result r;
+      if ((rc = fetch(&r))) return rc;
+      (*rounds)++;
+      *rhat = r.rhat;
+      if (r.rhat < thr) { *psi_out = psi; return PBN_OK; }
+      psi *= 2;
+    }
+  }
+
+  double elapsed_ms() {
+    float ms = 0.f;
+    cudaEventRecord(ev1, s);
+    cudaEventSynchronize(ev1);
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    return ms;
+  }
+};
+
+int check_query_common(const pbn_net *net, int64_t omega, int64_t psi0, double thr, int64_t max_length,
+                       int mode, const pbn_soi &soi) {
+  if (!net) return fail(PBN_ERR_INVALID, "NULL network");
+  if (omega < 2) return fail(PBN_ERR_INVALID, "omega must be >= 2");
+  if (psi0 < 2) return fail(PBN_ERR_INVALID, "psi0 must be >= 2");
+  if (!(thr > 0)) return fail(PBN_ERR_INVALID, "R-hat threshold");
+  if (max_length < 2 * psi0) return fail(PBN_ERR_INVALID, "max_length below 2 psi0");
+  if (mode != PBN_PERTURB_PER_NODE && mode != PBN_PERTURB_GLOBAL) return fail(PBN_ERR_INVALID, "perturb_mode");
+  if ((int64_t)((omega + 31) / 32) > (1ll << 31) - 1) return fail(PBN_ERR_UNSUPPORTED, "omega too large");
+  return check_soi(soi, net->dev.n, false);
+}
+
+}  // namespace
+
+extern "C" int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_query *q, pbn_two_state_report *out,
+                                      void *stream) {
+  if (!q || !out) return fail(PBN_ERR_INVALID, "NULL argument");
+  int rc = check_query_common(net, q->omega, q->psi0, q->rhat_threshold, q->max_length, q->perturb_mode, q->soi);
+  if (rc) return rc;
+  if (!(q->eps > 0 && q->r > 0 && q->s > 0 && q->s < 1)) return fail(PBN_ERR_INVALID, "eps, r, s out of range");
+  memset(out, 0, sizeof *out);
+  Query Q(net->dev, (cudaStream_t)stream);
+  Q.cfg.seed = q->seed;
+  Q.cfg.perturb_mode = q->perturb_mode;
+  Q.cfg.soi = q->soi;
+  if ((rc = Q.open(q->omega))) return rc;
+  int64_t psi;
+  if ((rc = Q.gelman_rubin(q->psi0, q->rhat_threshold, q->max_length, &psi, &out->rhat, &out->gr_rounds))) return rc;
+  out->gr_psi = psi;
+  const int64_t omega = q->omega;
+  pbn_two_state_result r;
+  memset(&r, 0, sizeof r);
+  for (;;) {      // burn-in check (Alg. 3: M against psi)
+    for (;;) {    // sample-size check (Alg. 3: N against the merged sample)
+      int64_t n = Q.ch.length - psi;
+      if (n < 2) {
+        if (psi + 2 > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "two-state: length cap");
+        if ((rc = Q.extend_to(psi + 2, psi))) return rc;
+        continue;
+      }
+      CUDA_TRY(pbn::launch_two_state(Q.ch, psi - Q.ch.bits_base, n, q->eps, q->r, q->s,
+                                     (pbn_two_state_result *)Q.d_res, Q.sc, Q.s),
+               "two-state");
+      Q.stat_launched(1);
+      if ((rc = Q.fetch(&r))) return rc;
+      out->ts_rounds++;
+      if (r.status == PBN_ERR_INSUFFICIENT) {
+        if (Q.ch.length + n > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "two-state: no transitions below the length cap");
+        if ((rc = Q.extend_to(Q.ch.length + n, psi))) return rc;
+        continue;
+      }
+      if (r.status != PBN_OK) return fail(r.status, "two-state chain is periodic (alpha = beta = 1)");
+      const int64_t deficit = r.N - omega * n;
+      if (deficit <= 0) break;
+      const int64_t extend_by = (deficit + omega - 1) / omega;
+      if (Q.ch.length + extend_by > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "two-state: length cap");
+      if ((rc = Q.extend_to(Q.ch.length + extend_by, psi))) return rc;
+    }
+    if (r.M > psi) { psi = r.M; continue; }
+    break;
+  }
+  out->prob = r.prob;
+  out->alpha = r.alpha;
+  out->beta = r.beta;
+  out->M = r.M;
+  out->N = r.N;
+  out->ones = r.ones;
+  out->n4[0] = r.n00; out->n4[1] = r.n01; out->n4[2] = r.n10; out->n4[3] = r.n11;
+  out->psi = psi;
+  out->length = Q.ch.length;
+  out->sample_size = omega * (Q.ch.length - psi);
+  out->chain_node_updates = omega * Q.ch.length * (int64_t)net->dev.n;
+  out->device_ms = Q.elapsed_ms();
+  out->sim_ms = Q.sim_ms();
+  out->sim_launches = Q.sim_launches;
+  out->kernel_launches = Q.kernel_launches;
+  out->sim_items = Q.sim_items;
+  out->d2h_bytes = Q.d2h_bytes;
+  return PBN_OK;
+}
+
+extern "C" int pbn_estimate_skart(const pbn_net *net, const pbn_skart_query *q, pbn_skart_report *out, void *stream) {
+  if (!q || !out) return fail(PBN_ERR_INVALID, "NULL argument");
+  int rc = check_query_common(net, q->omega, q->psi0, q->rhat_threshold, q->max_length, q->perturb_mode, q->soi);
+  if (rc) return rc;
+  if (!(q->H_star > 0 && q->alpha > 0 && q->alpha < 1)) return fail(PBN_ERR_INVALID, "H_star, alpha");
+  memset(out, 0, sizeof *out);
+  Query Q(net->dev, (cudaStream_t)stream);
+  Q.cfg.seed = q->seed;
+  Q.cfg.perturb_mode = q->perturb_mode;
+  Q.cfg.soi = q->soi;
+  if ((rc = Q.open(q->omega))) return rc;
+  int64_t psi;
+  if ((rc = Q.gelman_rubin(q->psi0, q->rhat_threshold, q->max_length, &psi, &out->rhat, &out->gr_rounds))) return rc;
+  const int64_t omega = q->omega;
+  const int64_t start = psi;  // the first psi samples of every chain are skipped
+  auto cdiv = [](int64_t a, int64_t b) { return (a + b - 1) / b; };
+  int64_t eta = cdiv(1280, omega) * omega;
+  // initial skewness of all eta samples: batch size 1, one batch per sample
+  if ((rc = Q.extend_to(start + eta / omega, start))) return rc;
+  pbn_skart_result sk;
+  CUDA_TRY(pbn::launch_skart(Q.ch, start - Q.ch.bits_base, 1, eta / omega, 0, q->alpha, 0.20,
+                             (pbn_skart_result *)Q.d_res, Q.sc, Q.s),
+           "Skart");
+  Q.stat_launched(2);
+  if ((rc = Q.fetch(&sk))) return rc;
+  int64_t kappa = fabs(sk.skew) > 4.0 ? 16 : 1;
+  int64_t p = cdiv(eta, omega) * omega;
+  eta = kappa * p;
+  int64_t d = 0;
+  const double alpha_ran = 0.20;
+  for (;;) {  // randomness test loop
+    if (start + eta / omega > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "Skart: length cap");
+    if ((rc = Q.extend_to(start + eta / omega, start))) return rc;
+    CUDA_TRY(pbn::launch_skart(Q.ch, start - Q.ch.bits_base, kappa, p / omega, d, q->alpha, alpha_ran,
+                               (pbn_skart_result *)Q.d_res, Q.sc, Q.s),
+             "Skart");
+    Q.stat_launched(2);
+    if ((rc = Q.fetch(&sk))) return rc;
+    out->rand_rounds++;
+    if (sk.vn_pass) break;
+    d += 1;
+    if (d > 10) {
+      d = 0;
+      kappa = (int64_t)ceil(sqrt(2.0) * (double)kappa);
+      p = (int64_t)ceil(0.9 * (double)p);
+    }
+    p = cdiv(p, omega) * omega;
+    eta = kappa * p;
+  }
+  out->spacer = d;
+  for (;;) {  // CI loop
+    if (start + eta / omega > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "Skart: length cap");
+    if (kappa > (1ll << 30)) return fail(PBN_ERR_UNSUPPORTED, "Skart batch size above 2^30");
+    if ((rc = Q.extend_to(start + eta / omega, start))) return rc;
+    CUDA_TRY(pbn::launch_skart(Q.ch, start - Q.ch.bits_base, kappa, p / omega, 0, q->alpha, alpha_ran,
+                               (pbn_skart_result *)Q.d_res, Q.sc, Q.s),
+             "Skart");
+    Q.stat_launched(2);
+    if ((rc = Q.fetch(&sk))) return rc;
+    out->ci_rounds++;
+    out->mean = sk.mean; out->ci_lo = sk.ci_lo; out->ci_hi = sk.ci_hi; out->H = sk.H;
+    out->var = sk.var; out->skew = sk.skew; out->phi = sk.phi;
+    const double Hs = q->relative ? q->H_star * fabs(sk.mean) : q->H_star;
+    if (!(sk.H > Hs)) break;
+    const double f = (sk.H / Hs) * (sk.H / Hs);
+    const int64_t pmax = p > 1024 ? p : 1024;
+    const double pf = ceil(f * (double)p);
+    const int64_t p1 = pf > (double)pmax ? pmax : (int64_t)pf;
+    int64_t k1 = (int64_t)ceil((double)kappa * f * (double)p / (double)p1);
+    if (k1 < kappa) k1 = kappa;
+    kappa = k1;
+    p = cdiv(p1, omega) * omega;
+    eta = kappa * p;
+  }
+  out->psi = psi;
+  out->length = Q.ch.length;
+  out->kappa = kappa;
+  out->batches = p;
+  out->sample_size = kappa * p;
+  out->chain_node_updates = omega * Q.ch.length * (int64_t)net->dev.n;
+  out->device_ms = Q.elapsed_ms();
+  out->sim_ms = Q.sim_ms();
+  out->sim_launches = Q.sim_launches;
+  out->kernel_launches = Q.kernel_launches;
+  out->sim_items = Q.sim_items;
+  out->d2h_bytes = Q.d2h_bytes;
+  return PBN_OK;
+}

@@ -1,0 +1,117 @@
+// Internal declarations of the GB300 PBN engine (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pbn.h"
+
+namespace pbn {
+
+constexpr int kMaxL = PBN_MAX_FUNCTIONS_PER_NODE;  // functions per node (thresholds per node incl. P32)
+constexpr int kMaxSoi = PBN_MAX_SOI;
+
+// Device tables of one network (built by pbn_load).
+//  node record (processing order r):  bits 0-11 node id, 12-15 l-1, 16-31 first function
+//  function record (uint4):
+//    x = truth table
+//    y = upper category bound T_j (unused for the last function of a node)
+//    z = p0 | p1 << 12 | (p4 & 0xFF) << 24
+//    w = p2 | p3 << 12 | (p4 >> 8) << 24 | k << 28
+struct NetDev {
+  int n = 0, F = 0;
+  uint32_t P32 = 0;
+  int max_l = 0;
+  uint32_t *d_node = nullptr;
+  uint4 *d_fn = nullptr;
+  int64_t table_bytes = 0;
+};
+
+__host__ __device__ __forceinline__ int node_id(uint32_t rec) { return (int)(rec & 0xFFFu); }
+__host__ __device__ __forceinline__ int node_l(uint32_t rec) { return (int)((rec >> 12) & 0xFu) + 1; }
+__host__ __device__ __forceinline__ int node_f0(uint32_t rec) { return (int)(rec >> 16); }
+__host__ __device__ __forceinline__ int fn_k(uint4 r) { return (int)(r.w >> 28); }
+
+// Philox4x32-10 round constants (Salmon et al., SC'11).
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
+// Round keys k_r = key + r * W, r = 0..9, precomputed on the host.
+struct RoundKeys {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+inline RoundKeys make_round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; r++) {
+    rk.k0[r] = a;
+    rk.k1[r] = b;
+    a += kPhiloxW0;
+    b += kPhiloxW1;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys &rk) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    uint64_t p0 = (uint64_t)kPhiloxM0 * c.x;
+    uint64_t p1 = (uint64_t)kPhiloxM1 * c.z;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
+  }
+  return c;
+}
+
+// Simulation launch arguments (passed by value, lives in the parameter bank).
+struct SimArgs {
+  RoundKeys rk;
+  const uint32_t *node;
+  const uint4 *fn;
+  uint32_t *state;
+  uint32_t *bits;
+  int64_t bits_cap;
+  int64_t col0;          // bits column of the first simulated position (may be < 0)
+  int64_t omega;
+  uint64_t t0;           // first transition index
+  int n, F, G;
+  int steps;
+  int gpb;               // chain groups per block
+  uint32_t P32;
+  int tables_in_smem;
+  int soi_size;
+  uint16_t soi_node[kMaxSoi];
+  uint32_t soi_val;      // bit m = required value of soi_node[m]
+};
+
+// Host-side launchers (defined in pbn_sim.cu / pbn_stats.cu).
+cudaError_t launch_init(const NetDev &net, uint64_t seed, uint32_t *state, int64_t omega, cudaStream_t s);
+cudaError_t launch_sim(const SimArgs &a, int mode, int threads, size_t smem, cudaStream_t s);
+size_t sim_smem_bytes(int n, int F, int gpb, int mode, bool tables_in_smem);
+int sim_max_smem();
+
+struct StatsScratch {
+  // device scratch for the reductions: block partials + a ticket counter
+  unsigned long long *partials = nullptr;  // [kMaxStatBlocks * 8]
+  unsigned int *ticket = nullptr;
+  int32_t *batch = nullptr;               // Skart batch sums
+  int64_t batch_cap = 0;
+};
+constexpr int kMaxStatBlocks = 512;
+
+cudaError_t scratch_init(StatsScratch &sc, cudaStream_t s);
+void scratch_free(StatsScratch &sc);
+cudaError_t scratch_reserve_batches(StatsScratch &sc, int64_t count, cudaStream_t s);
+
+cudaError_t launch_gelman_rubin(const pbn_chains &ch, int64_t col, int64_t psi, pbn_gr_result *out,
+                                StatsScratch &sc, cudaStream_t s);
+cudaError_t launch_two_state(const pbn_chains &ch, int64_t col, int64_t len, double eps, double r, double sconf,
+                             pbn_two_state_result *out, StatsScratch &sc, cudaStream_t s);
+cudaError_t launch_skart(const pbn_chains &ch, int64_t col, int64_t kappa, int64_t bpc, int64_t spacer,
+                         double alpha_ci, double alpha_ran, pbn_skart_result *out, StatsScratch &sc,
+                         cudaStream_t s);
+
+}  // namespace pbn

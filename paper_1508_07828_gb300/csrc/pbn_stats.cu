@@ -1,0 +1,536 @@
+// Statistics of the indicator bitstream on sm_103a: Gelman & Rubin
+// (Sec. 4.1), the two-state Markov chain quantities (Sec. 3.1, Alg. 1 line 8)
+// and the Skart batch statistics (Sec. 3.2, Alg. 4).
+//
+// Every reduction is exact: integer counts (popc of bitstream words, warp
+// bit-transposes to per-chain words, warp shuffles, 64/128-bit block sums),
+// written as per-block partials; the last block to finish (ticket counter)
+// folds the partials in a fixed order and does the few FP64 operations of
+// the statistic on one thread.  This translation unit is compiled without
+// FMA contraction so the FP64 formulas round the same way as plain C.
+#include <math.h>
+
+#include "pbn_internal.cuh"
+
+namespace pbn {
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+// ------------------------------------------------------------------ helpers
+
+// 32x32 bit transpose across a warp: lane j holds row j on entry; on exit
+// lane c holds column c (bit j = bit c of row j).  Each stage swaps the
+// off-diagonal s x s blocks between lanes j and j^s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0; k < 5; k++) {
+    const int s = 16 >> k;
+    const uint32_t m = masks[k];
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+  }
+  return x;
+}
+
+__device__ __forceinline__ uint32_t group_lanes(int64_t omega, int64_t g) {
+  int64_t rem = omega - g * 32;
+  return rem >= 32 ? 0xFFFFFFFFu : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+    lo = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+    hi = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+    v += ((u128)hi << 64) | lo;
+  }
+  return v;
+}
+
+// Block partials: NV 64-bit values per block.  Returns true in the last
+// block to finish, after which partials[0..gridDim.x) are all visible.
+template <int NV>
+__device__ bool publish_partials(const uint64_t (&vals)[NV], unsigned long long *partials, unsigned int *ticket) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; k++) partials[(size_t)blockIdx.x * NV + k] = vals[k];
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Block-wide sum of NV 64-bit values (wrapping; callers split 128-bit values).
+template <int NV>
+__device__ void block_sum64(uint64_t (&v)[NV]) {
+  __shared__ uint64_t red[32][NV];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; k++) v[k] = warp_sum<uint64_t>(v[k]);
+  if (lane == 0)
+    for (int k = 0; k < NV; k++) red[w][k] = v[k];
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = lane < nw ? red[lane][k] : 0ull;
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = warp_sum<uint64_t>(v[k]);
+  }
+  __syncthreads();
+}
+
+// -------------------------------------------------------- FP64 math pieces
+
+// Phi(-x) for x >= 0 through erfc, accurate in the tail.
+__device__ double upper_normal_tail(double x) { return 0.5 * erfc(x * 0.70710678118654752440); }
+
+// x >= 0 with Phi(-x) = tail (0 < tail <= 1/2): start from the rational
+// approximation of Abramowitz & Stegun 26.2.23 (|error| < 4.5e-4) and refine
+// with Newton steps on Phi(-x), whose derivative is -pdf(x).
+__device__ double normal_tail_quantile(double tail) {
+  double x = sqrt(-2.0 * log(tail));
+  x = x - (2.515517 + 0.802853 * x + 0.010328 * x * x) /
+              (1.0 + 1.432788 * x + 0.189269 * x * x + 0.001308 * x * x * x);
+  if (x < 0.0) x = 0.0;
+  for (int it = 0; it < 60; it++) {
+    const double q = upper_normal_tail(x);
+    const double pdf = 0.39894228040143267794 * exp(-0.5 * x * x);
+    const double step = (q - tail) / pdf;
+    x += step;
+    if (fabs(step) <= 4e-16 * fmax(1.0, x)) break;
+  }
+  return x;
+}
+
+__device__ double normal_quantile(double q) {
+  if (q == 0.5) return 0.0;
+  return q < 0.5 ? -normal_tail_quantile(q) : normal_tail_quantile(1.0 - q);
+}
+
+// ln Gamma(a+b) - ln Gamma(a); for large a by differencing Stirling's series.
+__device__ double ln_gamma_ratio(double a, double b) {
+  if (a < 25.0) return lgamma(a + b) - lgamma(a);
+  auto tail = [](double z) {
+    const double iz = 1.0 / z, iz2 = iz * iz;
+    return iz * (1.0 / 12.0 - iz2 * (1.0 / 360.0 - iz2 * (1.0 / 1260.0 - iz2 * (1.0 / 1680.0))));
+  };
+  return (a - 0.5) * log1p(b / a) + b * log(a + b) - b + (tail(a + b) - tail(a));
+}
+
+// Continued fraction of the regularised incomplete beta function
+// (even/odd coefficients d_2m, d_2m+1), modified Lentz evaluation.
+__device__ double beta_cfrac(double a, double b, double x) {
+  const double tiny = 1e-300;
+  double f = 1.0, C = 1.0, D = 1.0 - (a + b) * x / (a + 1.0);
+  D = fabs(D) < tiny ? 1.0 / tiny : 1.0 / D;
+  f = D;
+  for (int m = 1; m < 20000; m++) {
+    const double dm = m;
+    const double e = dm * (b - dm) * x / ((a + 2.0 * dm - 1.0) * (a + 2.0 * dm));
+    D = 1.0 + e * D; D = fabs(D) < tiny ? 1.0 / tiny : 1.0 / D;
+    C = 1.0 + e / C; if (fabs(C) < tiny) C = tiny;
+    f *= C * D;
+    const double o = -(a + dm) * (a + b + dm) * x / ((a + 2.0 * dm) * (a + 2.0 * dm + 1.0));
+    D = 1.0 + o * D; D = fabs(D) < tiny ? 1.0 / tiny : 1.0 / D;
+    C = 1.0 + o / C; if (fabs(C) < tiny) C = tiny;
+    const double r = C * D;
+    f *= r;
+    if (fabs(r - 1.0) < 2e-16) break;
+  }
+  return f;
+}
+
+// P(|T| > t) / 2 for Student t with nu degrees of freedom (t >= 0):
+// I_x(nu/2, 1/2) / 2 with x = nu/(nu + t^2), 1 - x = t^2/(nu + t^2).
+__device__ double student_upper_tail(double t, double nu) {
+  const double a = 0.5 * nu, b = 0.5;
+  const double x = nu / (nu + t * t), y = (t * t) / (nu + t * t);
+  if (y <= 0.0) return 0.5;
+  const double lnx = x > 0.5 ? log1p(-y) : log(x);
+  const double front = exp(ln_gamma_ratio(a, b) - lgamma(b) + a * lnx + b * log(y));
+  double I;
+  if (x < (a + 1.0) / (a + b + 2.0)) I = front * beta_cfrac(a, b, x) / a;
+  else I = 1.0 - front * beta_cfrac(b, a, y) / b;
+  return 0.5 * I;
+}
+
+// Student t quantile: Newton on the upper tail from the normal quantile.
+__device__ double student_quantile(double q, double nu) {
+  if (q == 0.5) return 0.0;
+  const double tail = q < 0.5 ? q : 1.0 - q;
+  double t = normal_tail_quantile(tail);
+  // first term of the Cornish-Fisher expansion of t in z for a closer start
+  t = t + (t * t * t + t) / (4.0 * nu);
+  const double lc = ln_gamma_ratio(0.5 * nu, 0.5) - 0.5 * log(nu * 3.14159265358979323846);
+  for (int it = 0; it < 100; it++) {
+    const double pdf = exp(lc - 0.5 * (nu + 1.0) * log1p(t * t / nu));
+    const double step = (student_upper_tail(t, nu) - tail) / pdf;
+    t += step;
+    if (t < 0.0) t = 0.0;
+    if (fabs(step) <= 4e-16 * fmax(1.0, t)) break;
+  }
+  return q < 0.5 ? -t : t;
+}
+
+// ------------------------------------------------------------ Gelman-Rubin
+
+__global__ void __launch_bounds__(256) gr_kernel(const uint32_t *bits, int64_t cap, int64_t col, int64_t psi,
+                                                 int64_t omega, int G, unsigned long long *partials,
+                                                 unsigned int *ticket, pbn_gr_result *out) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  uint64_t acc[3] = {0, 0, 0};  // S1, S2 lo, S2 hi
+  for (int64_t g = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); g < G; g += (int64_t)gridDim.x * wpb) {
+    const uint32_t *row = bits + (size_t)g * cap + col;
+    uint32_t cnt = 0;
+    for (int64_t j = 0; j < psi; j += 32) {
+      const uint32_t w = (j + lane < psi) ? row[j + lane] : 0u;
+      cnt += __popc(warp_transpose32(w, lane));
+    }
+    if (!((group_lanes(omega, g) >> lane) & 1u)) cnt = 0;
+    const uint64_t s1 = warp_sum<uint64_t>(cnt);
+    const u128 s2 = warp_sum_u128((u128)((uint64_t)cnt * cnt));
+    if (lane == 0) {
+      acc[0] += s1;
+      u128 t = ((u128)acc[2] << 64 | acc[1]) + s2;
+      acc[1] = (uint64_t)t;
+      acc[2] = (uint64_t)(t >> 64);
+    }
+  }
+  // block sum of (S1, S2) where S2 is held as 128-bit (lo, hi) pairs
+  __shared__ u128 red2[32];
+  __shared__ uint64_t red1[32];
+  const int w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red1[w] = acc[0];
+    red2[w] = ((u128)acc[2] << 64) | acc[1];
+  }
+  __syncthreads();
+  uint64_t part[3] = {0, 0, 0};
+  if (threadIdx.x == 0) {
+    uint64_t s1 = 0;
+    u128 s2 = 0;
+    for (int k = 0; k < wpb; k++) { s1 += red1[k]; s2 += red2[k]; }
+    part[0] = s1; part[1] = (uint64_t)s2; part[2] = (uint64_t)(s2 >> 64);
+  }
+  if (!publish_partials<3>(part, partials, ticket)) return;
+  if (threadIdx.x != 0) return;
+  uint64_t S1 = 0;
+  u128 S2 = 0;
+  for (unsigned b = 0; b < gridDim.x; b++) {
+    S1 += partials[(size_t)b * 3];
+    S2 += ((u128)partials[(size_t)b * 3 + 2] << 64) | partials[(size_t)b * 3 + 1];
+  }
+  *ticket = 0u;
+  const double p = (double)psi, w_ = (double)omega;
+  // W = (psi S1 - S2) / (omega psi (psi-1));  B = (omega S2 - S1^2) / (omega (omega-1) psi)
+  const i128 wnum = (i128)((u128)psi * S1) - (i128)S2;
+  const i128 bnum = (i128)((u128)omega * S2) - (i128)((u128)S1 * S1);
+  const double W = (double)wnum / (w_ * p * (p - 1.0));
+  const double B = (double)bnum / (w_ * (w_ - 1.0) * p);
+  const double sigma2 = (1.0 - 1.0 / p) * W + B / p;
+  pbn_gr_result r;
+  r.W = W;
+  r.B = B;
+  r.sigma2 = sigma2;
+  r.rhat = (W > 0.0) ? sqrt(sigma2 / W) : (double)INFINITY;
+  r.S1 = S1;
+  r.S2_lo = (uint64_t)S2;
+  r.S2_hi = (uint64_t)(S2 >> 64);
+  *out = r;
+}
+
+// --------------------------------------------------------------- two-state
+
+__device__ void two_state_formulas(pbn_two_state_result &r, int64_t omega, int64_t len, double eps, double rr,
+                                   double s) {
+  r.status = PBN_OK;
+  r.alpha = r.beta = 0.0;
+  r.M = r.N = 0;
+  r.prob = (double)r.ones / ((double)omega * (double)len);
+  if (len < 2 || r.n01 == 0 || r.n10 == 0) { r.status = PBN_ERR_INSUFFICIENT; return; }
+  const double a = (double)r.n01 / (double)(r.n00 + r.n01);
+  const double b = (double)r.n10 / (double)(r.n10 + r.n11);
+  r.alpha = a;
+  r.beta = b;
+  const double z = normal_quantile(0.5 * (1.0 + s));
+  const double apb = a + b;
+  const double Nreal = a * b * (2.0 - a - b) / (apb * apb * apb) * (z * z) / (rr * rr);
+  r.N = (int64_t)ceil(Nreal);
+  const double lam = fabs(1.0 - a - b);
+  if (lam == 0.0) { r.M = 0; return; }
+  if (lam >= 1.0) { r.status = PBN_ERR_NOT_CONVERGED; return; }
+  double Mreal = log(eps * apb / (a > b ? a : b)) / log(lam);
+  if (Mreal < 0.0) Mreal = 0.0;
+  r.M = (int64_t)ceil(Mreal);
+}
+
+__global__ void __launch_bounds__(256) two_state_kernel(const uint32_t *bits, int64_t cap, int64_t col,
+                                                        int64_t len, int64_t omega, int G, double eps, double rr,
+                                                        double s, unsigned long long *partials,
+                                                        unsigned int *ticket, pbn_two_state_result *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t chunks = (len + 31) / 32;
+  const int64_t items = (int64_t)G * chunks;
+  uint64_t v[4] = {0, 0, 0, 0};  // n11, from-ones, to-ones, ones
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = wid; it < items; it += nwarps) {
+    const int64_t g = it / chunks, ch = it - g * chunks;
+    const uint32_t vm = group_lanes(omega, g);
+    const uint32_t *row = bits + (size_t)g * cap + col;
+    const int64_t j = ch * 32 + lane;  // window position of this lane's word
+    const uint32_t w = j < len ? (row[j] & vm) : 0u;
+    uint32_t nx = __shfl_down_sync(0xFFFFFFFFu, w, 1);
+    if (lane == 31) nx = (j + 1 < len) ? (row[j + 1] & vm) : 0u;
+    const bool pair = (j + 1 < len);
+    v[3] += __popc(w);
+    if (pair) {
+      v[0] += __popc(w & nx);
+      v[1] += __popc(w);
+      v[2] += __popc(nx);
+    }
+  }
+  block_sum64<4>(v);
+  if (!publish_partials<4>(v, partials, ticket)) return;
+  if (threadIdx.x != 0) return;
+  uint64_t t[4] = {0, 0, 0, 0};
+  for (unsigned b = 0; b < gridDim.x; b++)
+    for (int k = 0; k < 4; k++) t[k] += partials[(size_t)b * 4 + k];
+  *ticket = 0u;
+  pbn_two_state_result r;
+  r.n11 = (int64_t)t[0];
+  r.n10 = (int64_t)t[1] - r.n11;
+  r.n01 = (int64_t)t[2] - r.n11;
+  r.n00 = (len >= 1 ? omega * (len - 1) : 0) - r.n11 - r.n10 - r.n01;
+  r.ones = (int64_t)t[3];
+  r.pad = 0;
+  two_state_formulas(r, omega, len, eps, rr, s);
+  *out = r;
+}
+
+// ------------------------------------------------------------------- Skart
+
+// Batch sums: chain c, batch j (j < bpc) covers window columns
+// [j*kappa, (j+1)*kappa); out[c * bpc + j].
+__global__ void __launch_bounds__(256) skart_batch_kernel(const uint32_t *bits, int64_t cap, int64_t col,
+                                                          int64_t kappa, int64_t bpc, int64_t omega, int G,
+                                                          int32_t *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t items = (int64_t)G * bpc;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = wid; it < items; it += nwarps) {
+    const int64_t g = it / bpc, j = it - g * bpc;
+    const uint32_t *row = bits + (size_t)g * cap + col + j * kappa;
+    uint32_t cnt = 0;
+    for (int64_t q = 0; q < kappa; q += 32) {
+      const uint32_t w = (q + lane < kappa) ? row[q + lane] : 0u;
+      cnt += __popc(warp_transpose32(w, lane));
+    }
+    const int64_t c = g * 32 + lane;
+    if (c < omega) out[c * bpc + j] = (int32_t)cnt;
+  }
+}
+
+// Moments of the batch sums and the Skart statistics, one block.
+__global__ void __launch_bounds__(1024) skart_stats_kernel(const int32_t *bs, int64_t omega, int64_t bpc,
+                                                           int64_t kappa, int64_t spacer, double alpha_ci,
+                                                           double alpha_ran, pbn_skart_result *out) {
+  const int64_t K = omega * bpc;
+  __shared__ long long s_c0;
+  // pass 1: total -> integer shift c0 = round(mean batch sum)
+  {
+    uint64_t v[1] = {0};
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) v[0] += (uint64_t)bs[k];
+    block_sum64<1>(v);
+    if (threadIdx.x == 0) s_c0 = (long long)((v[0] + (uint64_t)K / 2) / (uint64_t)K);
+    __syncthreads();
+  }
+  const long long c0 = s_c0;
+  const int64_t per = bpc / (spacer + 1);  // retained (spaced) batches per chain
+  // pass 2: shifted moments (exact, 128-bit)
+  i128 S1 = 0, S2 = 0, S3 = 0, Q = 0, Fst = 0, Lst = 0, T1 = 0, T2 = 0, D2 = 0;
+  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+    const int64_t c = k / bpc, j = k - c * bpc;
+    const i128 d = (i128)((long long)bs[k] - c0);
+    S1 += d; S2 += d * d; S3 += d * d * d;
+    if (j + 1 < bpc) Q += d * (i128)((long long)bs[k + 1] - c0);
+    if (j == 0) Fst += d;
+    if (j == bpc - 1) Lst += d;
+    if (j % (spacer + 1) == spacer && j / (spacer + 1) < per) {
+      T1 += d; T2 += d * d;
+      const int64_t jn = j + spacer + 1;
+      if (jn / (spacer + 1) < per) {
+        const i128 e = (i128)((long long)bs[c * bpc + jn] - c0) - d;
+        D2 += e * e;
+      }
+    }
+  }
+  __shared__ i128 red[32][9];
+  i128 vals[9] = {S1, S2, S3, Q, Fst, Lst, T1, T2, D2};
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 9; q++) {
+    i128 x = vals[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      uint64_t lo = (uint64_t)x, hi = (uint64_t)((u128)x >> 64);
+      lo = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+      hi = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+      x += (i128)(((u128)hi << 64) | lo);
+    }
+    if (lane == 0) red[w][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int q = 0; q < 9; q++) {
+    i128 x = 0;
+    for (int k = 0; k < nw; k++) x += red[k][q];
+    vals[q] = x;
+  }
+  const double Kd = (double)K, kap = (double)kappa;
+  const double m1 = (double)vals[0] / Kd;            // mean shifted batch sum
+  const double r2 = (double)vals[1] / Kd, r3 = (double)vals[2] / Kd;
+  const double m2 = r2 - m1 * m1;                    // population variance (batch-sum units)
+  const double m3 = r3 - 3.0 * m1 * r2 + 2.0 * m1 * m1 * m1;
+  pbn_skart_result res;
+  res.batches = K;
+  res.mean = ((double)c0 + m1) / kap;
+  res.var = (K > 1) ? m2 * Kd / (Kd - 1.0) / (kap * kap) : 0.0;
+  res.skew = m2 > 0.0 ? m3 / pow(m2, 1.5) : 0.0;
+  // pooled within-chain lag-1 autocorrelation
+  const int64_t P = omega * (bpc - 1);
+  double phi = 0.0;
+  if (P > 0 && m2 > 0.0) {
+    const double lsum = (double)(vals[0] - vals[5]), rsum = (double)(vals[0] - vals[4]);
+    const double cov = ((double)vals[3] - m1 * (lsum + rsum) + (double)P * m1 * m1) / (double)P;
+    phi = cov / m2;
+  }
+  if (phi > 0.999) phi = 0.999;
+  if (phi < -0.999) phi = -0.999;
+  res.phi = phi;
+  res.A = (1.0 + phi) / (1.0 - phi);
+  const double beta = res.skew / (6.0 * sqrt(Kd));
+  const double tu = student_quantile(1.0 - alpha_ci / 2.0, Kd - 1.0);
+  const double tl = -tu;
+  const double au = cbrt(1.0 + 6.0 * beta * (tu - beta));
+  const double al = cbrt(1.0 + 6.0 * beta * (tl - beta));
+  const double Gu = 3.0 * (tu - beta) / (au * au + au + 1.0);
+  const double Gl = 3.0 * (tl - beta) / (al * al + al + 1.0);
+  const double se = sqrt(res.A * res.var / Kd);
+  res.ci_lo = res.mean - Gu * se;
+  res.ci_hi = res.mean - Gl * se;
+  res.H = fmax(res.mean - res.ci_lo, res.ci_hi - res.mean);
+  // von Neumann randomness test on the spaced batch means
+  const int64_t Kp = per * omega, Pp = per > 1 ? (per - 1) * omega : 0;
+  res.vn_stat = 0.0;
+  res.vn_pass = 1;
+  if (Pp > 0 && Kp >= 3) {
+    const double t1 = (double)vals[6], t2 = (double)vals[7];
+    const double ss = t2 - t1 * t1 / (double)Kp;
+    if (ss > 0.0) {
+      const double C = 1.0 - ((double)(Kp - 1) / (double)Pp) * (double)vals[8] / (2.0 * ss);
+      const double mm = (double)(Pp + 1);
+      const double crit = normal_quantile(1.0 - alpha_ran) * sqrt((mm - 2.0) / (mm * mm - 1.0));
+      res.vn_stat = C;
+      res.vn_pass = C <= crit;
+    }
+  }
+  res.pad = 0;
+  *out = res;
+}
+
+// ---------------------------------------------------------------- launchers
+
+static int stat_blocks(int64_t work_warps, int wpb) {
+  int64_t b = (work_warps + wpb - 1) / wpb;
+  if (b < 1) b = 1;
+  if (b > kMaxStatBlocks) b = kMaxStatBlocks;
+  return (int)b;
+}
+
+cudaError_t scratch_init(StatsScratch &sc, cudaStream_t s) {
+  cudaError_t e = cudaMalloc(&sc.partials, sizeof(unsigned long long) * kMaxStatBlocks * 8);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&sc.ticket, sizeof(unsigned int));
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(sc.ticket, 0, sizeof(unsigned int), s);
+}
+
+void scratch_free(StatsScratch &sc) {
+  if (sc.partials) cudaFree(sc.partials);
+  if (sc.ticket) cudaFree(sc.ticket);
+  if (sc.batch) cudaFree(sc.batch);
+  sc = StatsScratch();
+}
+
+cudaError_t scratch_reserve_batches(StatsScratch &sc, int64_t count, cudaStream_t s) {
+  if (count <= sc.batch_cap) return cudaSuccess;
+  if (sc.batch) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    cudaFree(sc.batch);
+    sc.batch = nullptr;
+  }
+  int64_t cap = sc.batch_cap ? sc.batch_cap : 4096;
+  while (cap < count) cap *= 2;
+  cudaError_t e = cudaMalloc(&sc.batch, sizeof(int32_t) * cap);
+  if (e != cudaSuccess) { sc.batch_cap = 0; return e; }
+  sc.batch_cap = cap;
+  return cudaSuccess;
+}
+
+cudaError_t launch_gelman_rubin(const pbn_chains &ch, int64_t col, int64_t psi, pbn_gr_result *out,
+                                StatsScratch &sc, cudaStream_t s) {
+  const int G = (int)((ch.omega + 31) / 32);
+  const int threads = 256;
+  const int blocks = stat_blocks(G, threads / 32);
+  gr_kernel<<<blocks, threads, 0, s>>>(ch.bits, ch.bits_cap, col, psi, ch.omega, G, sc.partials, sc.ticket, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_two_state(const pbn_chains &ch, int64_t col, int64_t len, double eps, double r, double sconf,
+                             pbn_two_state_result *out, StatsScratch &sc, cudaStream_t s) {
+  const int G = (int)((ch.omega + 31) / 32);
+  const int threads = 256;
+  const int64_t warps = (int64_t)G * ((len + 31) / 32);
+  const int blocks = stat_blocks(warps, threads / 32);
+  two_state_kernel<<<blocks, threads, 0, s>>>(ch.bits, ch.bits_cap, col, len, ch.omega, G, eps, r, sconf,
+                                              sc.partials, sc.ticket, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_skart(const pbn_chains &ch, int64_t col, int64_t kappa, int64_t bpc, int64_t spacer,
+                         double alpha_ci, double alpha_ran, pbn_skart_result *out, StatsScratch &sc,
+                         cudaStream_t s) {
+  const int G = (int)((ch.omega + 31) / 32);
+  cudaError_t e = scratch_reserve_batches(sc, ch.omega * bpc, s);
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  int64_t blocks = ((int64_t)G * bpc + 7) / 8;
+  if (blocks > 65535) blocks = 65535;
+  if (blocks < 1) blocks = 1;
+  skart_batch_kernel<<<(unsigned)blocks, threads, 0, s>>>(ch.bits, ch.bits_cap, col, kappa, bpc, ch.omega, G,
+                                                          sc.batch);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  skart_stats_kernel<<<1, 1024, 0, s>>>(sc.batch, ch.omega, bpc, kappa, spacer, alpha_ci, alpha_ran, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pbn
