@@ -195,6 +195,27 @@ typedef struct pbn_skart_result {
 int pbn_skart(const pbn_chains *chains, int64_t start, int64_t kappa, int64_t batches_per_chain,
               int64_t spacer, double alpha_ci, double alpha_ran, pbn_skart_result *out, void *stream);
 
+/* Maximum omega * batches_per_chain of pbn_skart_static. */
+#define PBN_SKART_STATIC_MAX_BATCHES (1 << 18)
+
+/* pbn_skart without any device allocation.  The paper has no counterpart;
+ * this is for callers that cannot let a library call cudaMalloc, such as a
+ * host program that owns all device memory through its own allocator, or a
+ * latency-critical loop in which an allocation would stall the device.
+ * Computes exactly what pbn_skart computes, but keeps the per-batch sums in
+ * a fixed array of PBN_SKART_STATIC_MAX_BATCHES entries (1 MiB) inside the
+ * library's device image, which every GPU that loads the library holds until
+ * the process exits.  The caller still passes the chains and the result slot.
+ * The first call on a device looks up the array's device address (make that
+ * first call before any stream capture).  All calls share the one array:
+ * calls whose work overlaps on the GPU (different streams, or other host
+ * threads) race and must be serialised by the caller.  Each call overwrites
+ * every batch sum it reads, so nothing needs clearing between calls.
+ * Errors: PBN_ERR_UNSUPPORTED when omega * batches_per_chain exceeds
+ * PBN_SKART_STATIC_MAX_BATCHES, otherwise as pbn_skart. */
+int pbn_skart_static(const pbn_chains *chains, int64_t start, int64_t kappa, int64_t batches_per_chain,
+                     int64_t spacer, double alpha_ci, double alpha_ran, pbn_skart_result *out, void *stream);
+
 /* -------------------------------------------------------------- drivers */
 
 typedef struct pbn_two_state_query {

@@ -135,6 +135,7 @@ def lib():
             L.pbn_gelman_rubin.argtypes = [P(Chains), c_i64, c_i64, c_vp, c_vp]
             L.pbn_two_state.argtypes = [P(Chains), c_i64, c_i64, c_dbl, c_dbl, c_dbl, c_vp, c_vp]
             L.pbn_skart.argtypes = [P(Chains), c_i64, c_i64, c_i64, c_i64, c_dbl, c_dbl, c_vp, c_vp]
+            L.pbn_skart_static.argtypes = [P(Chains), c_i64, c_i64, c_i64, c_i64, c_dbl, c_dbl, c_vp, c_vp]
             L.pbn_estimate_two_state.argtypes = [c_vp, P(TwoStateQuery), P(TwoStateReport), c_vp]
             L.pbn_estimate_skart.argtypes = [c_vp, P(SkartQuery), P(SkartReport), c_vp]
             L.pbn_last_error.restype = ctypes.c_char_p
@@ -325,6 +326,18 @@ def pbn_two_state(chains: ChainSet, start: int, length: int, eps: float, r: floa
 def pbn_skart(chains: ChainSet, start: int, kappa: int, batches_per_chain: int, spacer: int, alpha_ci: float,
               alpha_ran: float = 0.20, stream=None) -> dict:
     res = _device_result(SkartResult, lambda p: _check(lib().pbn_skart(
+        ctypes.byref(chains.c), int(start), int(kappa), int(batches_per_chain), int(spacer), float(alpha_ci),
+        float(alpha_ran), p, _stream(stream))))
+    return _as_struct(SkartResult, res)
+
+
+def pbn_skart_static(chains: ChainSet, start: int, kappa: int, batches_per_chain: int, spacer: int,
+                     alpha_ci: float, alpha_ran: float = 0.20, stream=None) -> dict:
+    """pbn_skart for callers that cannot allocate device memory: the batch
+    sums live in a fixed array inside the library (see include/pbn.h), so the
+    call allocates nothing.  Calls that overlap on the GPU share that array
+    and must be serialised by the caller."""
+    res = _device_result(SkartResult, lambda p: _check(lib().pbn_skart_static(
         ctypes.byref(chains.c), int(start), int(kappa), int(batches_per_chain), int(spacer), float(alpha_ci),
         float(alpha_ran), p, _stream(stream))))
     return _as_struct(SkartResult, res)

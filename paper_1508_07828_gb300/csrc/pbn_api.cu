@@ -177,6 +177,8 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
 
 }  // namespace
 
+void pbn::set_last_error(const char *msg) { g_err = msg; }
+
 extern "C" {
 
 const char *pbn_last_error(void) { return g_err.c_str(); }

@@ -87,6 +87,9 @@ struct SimArgs {
   uint32_t soi_val;      // bit m = required value of soi_node[m]
 };
 
+// Sets the thread-local message returned by pbn_last_error (pbn_api.cu).
+void set_last_error(const char *msg);
+
 // Host-side launchers (defined in pbn_sim.cu / pbn_stats.cu).
 cudaError_t launch_init(const NetDev &net, uint64_t seed, uint32_t *state, int64_t omega, cudaStream_t s);
 cudaError_t launch_sim(const SimArgs &a, int mode, int threads, size_t smem, cudaStream_t s);
@@ -113,5 +116,9 @@ cudaError_t launch_two_state(const pbn_chains &ch, int64_t col, int64_t len, dou
 cudaError_t launch_skart(const pbn_chains &ch, int64_t col, int64_t kappa, int64_t bpc, int64_t spacer,
                          double alpha_ci, double alpha_ran, pbn_skart_result *out, StatsScratch &sc,
                          cudaStream_t s);
+// Same kernels with a caller-provided batch-sum buffer of at least omega * bpc entries.
+cudaError_t launch_skart_into(const pbn_chains &ch, int64_t col, int64_t kappa, int64_t bpc, int64_t spacer,
+                              double alpha_ci, double alpha_ran, pbn_skart_result *out, int32_t *batch,
+                              cudaStream_t s);
 
 }  // namespace pbn

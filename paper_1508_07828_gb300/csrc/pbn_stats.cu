@@ -533,4 +533,18 @@ cudaError_t launch_skart(const pbn_chains &ch, int64_t col, int64_t kappa, int64
   return cudaGetLastError();
 }
 
+cudaError_t launch_skart_into(const pbn_chains &ch, int64_t col, int64_t kappa, int64_t bpc, int64_t spacer,
+                              double alpha_ci, double alpha_ran, pbn_skart_result *out, int32_t *batch,
+                              cudaStream_t s) {
+  const int G = (int)((ch.omega + 31) / 32);
+  int64_t blocks = ((int64_t)G * bpc + 7) / 8;
+  if (blocks > 65535) blocks = 65535;
+  if (blocks < 1) blocks = 1;
+  skart_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(ch.bits, ch.bits_cap, col, kappa, bpc, ch.omega, G, batch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  skart_stats_kernel<<<1, 1024, 0, s>>>(batch, ch.omega, bpc, kappa, spacer, alpha_ci, alpha_ran, out);
+  return cudaGetLastError();
+}
+
 }  // namespace pbn
