@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sim-only", choices=["mid", "large"], default=None,
+                    help="time the simulation kernel alone on a workload (kernel benchmark / profiling case)")
+    ap.add_argument("--sim-steps", type=int, default=1024, help="transitions per launch in --sim-only")
+    ap.add_argument("--threads-per-item", type=int, default=0)
+    ap.add_argument("--blocks-per-round", type=int, default=0)
+    ap.add_argument("--groups-per-block", type=int, default=0)
     return ap.parse_args()
 
 
@@ -344,8 +350,62 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+def run_sim_only(args):
+    """The simulation kernel alone: omega chains advanced by --sim-steps
+    transitions per launch, CUDA events around each launch."""
+    import torch
+    import pbn_synth as S
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+    torch.cuda.set_device(0)
+    if args.sim_only == "mid":
+        net, soi, cfg = workload()
+        omega = cfg["omega"]
+    else:
+        net, nodes, cfg = S.large_config()
+        soi = S.StateOfInterest(nodes, np.ones(len(nodes), dtype=np.uint8))
+        omega = cfg["omega"]
+    N = P.pbn_load(net)
+    steps = args.sim_steps
+    cs = P.ChainSet(N, omega, bits_cap=steps)
+    P.pbn_init_chains(cs, 5)
+    launch = dict(threads_per_item=args.threads_per_item, blocks_per_round=args.blocks_per_round,
+                  groups_per_block=args.groups_per_block)
+    stream = torch.cuda.current_stream()
+
+    def one():
+        cs.c.bits_base = cs.c.length
+        P.pbn_run_chains(cs, steps, 5, P.PER_NODE, soi, **launch)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        a.record(stream)
+        one()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    upd = omega * steps * net.n
+    ops = algorithmic_ops_per_item(net).sum() * ((omega + 31) // 32) * steps
+    peak, sms, mhz, src = alu_peak_tops(0)
+    achieved = ops / (np.mean(ms) / 1e3) / 1e12
+    print(json.dumps({"mode": "sim-only", "workload": args.sim_only, "nodes": int(net.n), "chains": omega,
+                      "steps_per_launch": steps, "launches": args.steps, "ms_per_launch": float(np.mean(ms)),
+                      "ms_min": float(np.min(ms)), "updates_per_s": upd / (np.mean(ms) / 1e3),
+                      "ns_per_transition": 1e6 * float(np.mean(ms)) / steps,
+                      "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                                   "frac": achieved / peak},
+                      "launch": launch}))
+
+
 def main():
     args = parse()
+    if args.sim_only:
+        run_sim_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

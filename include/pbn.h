@@ -114,6 +114,8 @@ typedef struct pbn_run_cfg {
     pbn_soi soi;
     int32_t groups_per_block;   /* 0 = automatic */
     int32_t threads_per_block;  /* 0 = automatic */
+    int32_t threads_per_item;   /* threads sharing one (node, chain group) update: 1, 2, 4; 0 = automatic */
+    int32_t blocks_per_round;   /* Philox blocks per thread per round when threads_per_item = 1: 1, 2; 0 = auto */
 } pbn_run_cfg;
 
 /* ---------------------------------------------------------------- network */

@@ -66,7 +66,7 @@ class Chains(ctypes.Structure):
 
 class RunCfg(ctypes.Structure):
     _fields_ = [("seed", c_u64), ("perturb_mode", c_i32), ("soi", Soi), ("groups_per_block", c_i32),
-                ("threads_per_block", c_i32)]
+                ("threads_per_block", c_i32), ("threads_per_item", c_i32), ("blocks_per_round", c_i32)]
 
 
 class GrResult(ctypes.Structure):
@@ -283,8 +283,9 @@ class ChainSet:
         return b.reshape(self.G * 32, length)[: self.omega]
 
 
-def _cfg(seed, mode, soi_arg, groups_per_block=0, threads_per_block=0):
-    return RunCfg(int(seed), int(mode), soi_arg.struct, int(groups_per_block), int(threads_per_block))
+def _cfg(seed, mode, soi_arg, groups_per_block=0, threads_per_block=0, threads_per_item=0, blocks_per_round=0):
+    return RunCfg(int(seed), int(mode), soi_arg.struct, int(groups_per_block), int(threads_per_block),
+                  int(threads_per_item), int(blocks_per_round))
 
 
 def pbn_init_chains(chains: ChainSet, seed: int, mode: int = PER_NODE, stream=None):
@@ -294,9 +295,10 @@ def pbn_init_chains(chains: ChainSet, seed: int, mode: int = PER_NODE, stream=No
 
 
 def pbn_run_chains(chains: ChainSet, steps: int, seed: int, mode: int = PER_NODE, soi=None,
-                   groups_per_block: int = 0, threads_per_block: int = 0, stream=None):
+                   groups_per_block: int = 0, threads_per_block: int = 0, threads_per_item: int = 0,
+                   blocks_per_round: int = 0, stream=None):
     soi_arg = SoiArg(soi)
-    cfg = _cfg(seed, mode, soi_arg, groups_per_block, threads_per_block)
+    cfg = _cfg(seed, mode, soi_arg, groups_per_block, threads_per_block, threads_per_item, blocks_per_round)
     _check(lib().pbn_run_chains(chains.network.handle, ctypes.byref(cfg), ctypes.byref(chains.c), int(steps),
                                 _stream(stream)))
 

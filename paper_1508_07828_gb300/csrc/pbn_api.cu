@@ -96,12 +96,17 @@ int check_soi(const pbn_soi &soi, int n, bool allow_empty) {
 }
 
 struct LaunchPlan {
-  int gpb, threads;
+  int gpb, threads, T, BPR;
   size_t smem;
   bool tables_in_smem;
 };
 
-int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, int threads_req, LaunchPlan *p) {
+// Launch shape: chain groups per CTA from the group count and the SM count
+// (shared memory permitting); with fewer groups than SMs the step is
+// latency-bound, so 4 threads share an item (its Philox blocks run in
+// parallel); otherwise one thread per item with 2 blocks per round for ILP.
+int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, int threads_req, int T_req,
+                int BPR_req, LaunchPlan *p) {
   const int G = (int)((omega + 31) / 32);
   const int maxs = pbn::sim_max_smem();
   int gpb = gpb_req > 0 ? gpb_req : std::max(1, (G + sm_count() - 1) / sm_count());
@@ -114,11 +119,22 @@ int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, in
     if (gpb == 1) return fail(PBN_ERR_UNSUPPORTED, "chain state of one group does not fit shared memory");
     gpb = std::max(1, gpb / 2);
   }
-  int items = net.n * gpb;
-  int threads = threads_req > 0 ? threads_req : std::min(1024, std::max(32, (items + 31) / 32 * 32));
-  if (threads % 32 || threads > 1024) return fail(PBN_ERR_INVALID, "threads_per_block %d", threads);
+  int T = T_req;
+  if (T == 0) T = G < sm_count() ? (net.n * gpb * 4 <= 512 ? 4 : (net.n * gpb * 2 <= 512 ? 2 : 1)) : 1;
+  if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
+  int BPR = BPR_req ? BPR_req : 2;
+  if (T == 2) BPR = 2;
+  if (T == 4) BPR = 1;
+  if (BPR != 1 && BPR != 2) return fail(PBN_ERR_INVALID, "blocks_per_round %d (1 or 2)", BPR);
+  const int items = net.n * gpb;
+  const int tmax = T == 1 ? 1024 : 512;
+  int threads = threads_req > 0 ? threads_req : std::min(tmax, std::max(32, (items * T + 31) / 32 * 32));
+  if (threads % 32 || threads > tmax || threads < 32)
+    return fail(PBN_ERR_INVALID, "threads_per_block %d (a multiple of 32, at most %d here)", threads, tmax);
   p->gpb = gpb;
   p->threads = threads;
+  p->T = T;
+  p->BPR = BPR;
   return PBN_OK;
 }
 
@@ -161,7 +177,8 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
                                          (long long)ch.bits_cap, (long long)(ch.length + steps - 1));
   }
   LaunchPlan plan;
-  int rc = plan_launch(net, ch.omega, cfg.perturb_mode, cfg.groups_per_block, cfg.threads_per_block, &plan);
+  int rc = plan_launch(net, ch.omega, cfg.perturb_mode, cfg.groups_per_block, cfg.threads_per_block,
+                       cfg.threads_per_item, cfg.blocks_per_round, &plan);
   if (rc) return rc;
   // one launch covers at most 2^30 steps; the step counter itself is 64-bit
   const int64_t chunk = 1 << 30;
@@ -169,7 +186,8 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
     const int64_t k = std::min(chunk, steps - done);
     pbn::SimArgs a = make_args(net, cfg, ch, k, plan);
     if (!record) a.soi_size = 0;
-    CUDA_TRY(pbn::launch_sim(a, cfg.perturb_mode, plan.threads, plan.smem, s), "simulation launch");
+    CUDA_TRY(pbn::launch_sim(a, cfg.perturb_mode, plan.T, plan.BPR, plan.threads, plan.smem, s),
+             "simulation launch");
     ch.length += k;
   }
   return PBN_OK;
@@ -250,7 +268,8 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
         T = t > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)t;
       }
       uint4 r;
-      r.x = d->truth_table[f];
+      // bits at or above 2^k are not part of the function; the kernels rely on them being 0
+      r.x = k == 5 ? d->truth_table[f] : (d->truth_table[f] & ((1u << (1u << k)) - 1u));
       r.y = T;
       r.z = (uint32_t)par[0] | ((uint32_t)par[1] << 12) | (((uint32_t)par[4] & 0xFFu) << 24);
       r.w = (uint32_t)par[2] | ((uint32_t)par[3] << 12) | (((uint32_t)par[4] >> 8) << 24) | ((uint32_t)k << 28);

@@ -92,7 +92,9 @@ void set_last_error(const char *msg);
 
 // Host-side launchers (defined in pbn_sim.cu / pbn_stats.cu).
 cudaError_t launch_init(const NetDev &net, uint64_t seed, uint32_t *state, int64_t omega, cudaStream_t s);
-cudaError_t launch_sim(const SimArgs &a, int mode, int threads, size_t smem, cudaStream_t s);
+// T = threads per (node, group) item (1, 2 or 4); BPR = Philox blocks per
+// thread per round (T = 1: 1 or 2; T = 2 uses 2; T = 4 uses 1).
+cudaError_t launch_sim(const SimArgs &a, int mode, int T, int BPR, int threads, size_t smem, cudaStream_t s);
 size_t sim_smem_bytes(int n, int F, int gpb, int mode, bool tables_in_smem);
 int sim_max_smem();
 

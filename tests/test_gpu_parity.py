@@ -83,14 +83,32 @@ def test_trajectories_bit_exact(P, name, net, soi, omega, mode):
     assert np.array_equal(cs.indicator_numpy(0, t0), np.concatenate(inds, axis=1))
 
 
-@pytest.mark.parametrize("launch", [dict(groups_per_block=2), dict(groups_per_block=3, threads_per_block=64),
-                                    dict(threads_per_block=32)])
-def test_launch_shape_does_not_change_results(P, launch):
+LAUNCHES = [dict(groups_per_block=2), dict(groups_per_block=3, threads_per_block=64), dict(threads_per_block=32),
+            dict(threads_per_item=1, blocks_per_round=1), dict(threads_per_item=1, blocks_per_round=2),
+            dict(threads_per_item=2), dict(threads_per_item=4), dict(threads_per_item=4, groups_per_block=2),
+            dict(threads_per_item=2, threads_per_block=96)]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("launch", LAUNCHES, ids=[str(x) for x in LAUNCHES])
+def test_launch_shape_does_not_change_results(P, launch, mode):
     net, soi = S.mid_config()[:2]
-    a, _, sa = _gpu_run(P, net, soi, 200, 3, 0, [40])
-    b, _, sb = _gpu_run(P, net, soi, 200, 3, 0, [40], **launch)
+    a, _, sa = _gpu_run(P, net, soi, 200, 3, mode, [40])
+    b, _, sb = _gpu_run(P, net, soi, 200, 3, mode, [40], **launch)
     assert np.array_equal(sa[-1], sb[-1])
     assert np.array_equal(a.indicator_numpy(0, 40), b.indicator_numpy(0, 40))
+
+
+@pytest.mark.parametrize("launch", [dict(threads_per_item=1, blocks_per_round=1), dict(threads_per_item=2),
+                                    dict(threads_per_item=4)], ids=["t1b1", "t2", "t4"])
+@pytest.mark.parametrize("name", ["k0-mix", "l8", "scalefree-300", "high-p"])
+def test_item_thread_variants_bit_exact(P, name, launch):
+    net, soi, omega = next((x[1], x[2], x[3]) for x in NETS if x[0] == name)
+    for mode in (0, 1):
+        cs, init, states = _gpu_run(P, net, soi, omega, 77, mode, [33], **launch)
+        ref, ind = oracle.simulate(net, mode, 77, oracle.init_states(net, 77, omega), 0, 33, soi)
+        assert np.array_equal(states[-1], ref)
+        assert np.array_equal(cs.indicator_numpy(0, 33), ind)
 
 
 def test_max_nodes_and_max_soi(P):
