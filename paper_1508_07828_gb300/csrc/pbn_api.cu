@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -103,8 +104,8 @@ struct LaunchPlan {
 
 // Launch shape: chain groups per CTA from the group count and the SM count
 // (shared memory permitting); with fewer groups than SMs the step is
-// latency-bound, so 4 threads share an item (its Philox blocks run in
-// parallel); otherwise one thread per item with 2 blocks per round for ILP.
+// latency-bound, so 2 threads share an item (each runs 2 Philox blocks, in
+// parallel); otherwise one thread per item, one block per round.
 int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, int threads_req, int T_req,
                 int BPR_req, LaunchPlan *p) {
   const int G = (int)((omega + 31) / 32);
@@ -120,9 +121,9 @@ int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, in
     gpb = std::max(1, gpb / 2);
   }
   int T = T_req;
-  if (T == 0) T = G < sm_count() ? (net.n * gpb * 4 <= 512 ? 4 : (net.n * gpb * 2 <= 512 ? 2 : 1)) : 1;
+  if (T == 0) T = (G < sm_count() && net.n * gpb * 2 <= 512) ? 2 : 1;
   if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
-  int BPR = BPR_req ? BPR_req : 2;
+  int BPR = BPR_req ? BPR_req : 1;
   if (T == 2) BPR = 2;
   if (T == 4) BPR = 1;
   if (BPR != 1 && BPR != 2) return fail(PBN_ERR_INVALID, "blocks_per_round %d (1 or 2)", BPR);
@@ -391,70 +392,127 @@ int pbn_skart(const pbn_chains *ch, int64_t start, int64_t kappa, int64_t bpc, i
 
 namespace {
 
-// Chains owned by one driver call: state, a growing bitstream window and the
-// statistics scratch, all stream-ordered allocations.
+// Per-(device, stream) driver workspace, kept across queries so that a query
+// makes no allocation once the buffers have grown to its size: statistics
+// scratch, a device result slot with its pinned host copy, chain state, two
+// bitstream buffers (one is the copy target when the window must grow) and
+// a pool of timing events.  One driver query at a time per workspace.
+struct Workspace {
+  std::mutex mu;
+  pbn::StatsScratch sc;
+  void *d_res = nullptr;
+  void *h_res = nullptr;
+  uint32_t *state = nullptr;
+  size_t state_words = 0;
+  uint32_t *bits[2] = {nullptr, nullptr};
+  size_t bits_words[2] = {0, 0};
+  int cur_bits = 0;
+  std::vector<cudaEvent_t> events;
+  bool ready = false;
+
+  int setup(cudaStream_t s) {
+    if (ready) return PBN_OK;
+    CUDA_TRY(pbn::scratch_init(sc, s), "scratch");
+    CUDA_TRY(cudaMalloc(&d_res, 256), "result alloc");
+    CUDA_TRY(cudaMallocHost(&h_res, 256), "pinned alloc");
+    ready = true;
+    return PBN_OK;
+  }
+
+  int ensure(uint32_t *&buf, size_t &have, size_t words, cudaStream_t s, const char *what) {
+    if (words <= have) return PBN_OK;
+    if (buf) cudaFreeAsync(buf, s);
+    buf = nullptr;
+    have = 0;
+    size_t w = std::max<size_t>(words, 1024);
+    CUDA_TRY(cudaMallocAsync(&buf, w * sizeof(uint32_t), s), what);
+    have = w;
+    return PBN_OK;
+  }
+
+  cudaEvent_t event(size_t k) {
+    while (events.size() <= k) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      events.push_back(e);
+    }
+    return events[k];
+  }
+};
+
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, std::unique_ptr<Workspace>> g_ws;
+
+Workspace &workspace_for(cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  auto &slot = g_ws[std::make_pair(dev, s)];
+  if (!slot) slot.reset(new Workspace());
+  return *slot;
+}
+
+// Chains of one driver call on a borrowed workspace: state, a growing
+// bitstream window and the statistics scratch.
 struct Query {
   const pbn::NetDev &net;
   pbn_run_cfg cfg;
   cudaStream_t s;
+  Workspace &ws;
+  std::lock_guard<std::mutex> hold;
   pbn_chains ch;
-  pbn::StatsScratch sc;
-  void *d_res = nullptr;   // device result slot
-  void *h_res = nullptr;   // pinned host copy
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  std::vector<cudaEvent_t> sim_ev;   // start/stop pairs around simulation launches
+  pbn::StatsScratch &sc;
+  void *d_res = nullptr;
+  size_t n_events = 0;   // events 0, 1: whole query; then start/stop pairs of simulation launches
   int64_t sim_launches = 0, kernel_launches = 0, sim_items = 0, d2h_bytes = 0;
 
-  Query(const pbn::NetDev &n, cudaStream_t st) : net(n), s(st) {
+  Query(const pbn::NetDev &n, cudaStream_t st)
+      : net(n), s(st), ws(workspace_for(st)), hold(ws.mu), sc(ws.sc) {
     memset(&cfg, 0, sizeof cfg);
     memset(&ch, 0, sizeof ch);
   }
-  ~Query() {
-    if (ch.state) cudaFreeAsync(ch.state, s);
-    if (ch.bits) cudaFreeAsync(ch.bits, s);
-    if (d_res) cudaFreeAsync(d_res, s);
-    cudaStreamSynchronize(s);
-    pbn::scratch_free(sc);
-    if (h_res) cudaFreeHost(h_res);
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    for (cudaEvent_t e : sim_ev) cudaEventDestroy(e);
-  }
 
   int open(int64_t omega) {
+    int rc = ws.setup(s);
+    if (rc) return rc;
+    d_res = ws.d_res;
     ch.omega = omega;
     const int G = (int)((omega + 31) / 32);
-    CUDA_TRY(cudaMallocAsync(&ch.state, sizeof(uint32_t) * (size_t)G * net.n, s), "state alloc");
-    CUDA_TRY(cudaMallocAsync(&d_res, 256, s), "result alloc");
-    CUDA_TRY(cudaMallocHost(&h_res, 256), "pinned alloc");
-    CUDA_TRY(pbn::scratch_init(sc, s), "scratch");
-    CUDA_TRY(cudaEventCreate(&ev0), "event");
-    CUDA_TRY(cudaEventCreate(&ev1), "event");
-    CUDA_TRY(cudaEventRecord(ev0, s), "event");
+    if ((rc = ws.ensure(ws.state, ws.state_words, (size_t)G * net.n, s, "state alloc"))) return rc;
+    ch.state = ws.state;
+    cudaEvent_t e0 = ws.event(0), e1 = ws.event(1);
+    if (!e0 || !e1) return fail(PBN_ERR_CUDA, "event creation failed");
+    n_events = 2;
+    CUDA_TRY(cudaEventRecord(e0, s), "event");
     CUDA_TRY(pbn::launch_init(net, cfg.seed, ch.state, omega, s), "init");
     kernel_launches++;
     ch.length = 0;
     return PBN_OK;
   }
 
-  // Make the bitstream hold positions [base, upto): re-bases when nothing
-  // before `base` is needed any more, grows (copying the kept columns) otherwise.
+  // Make the bitstream hold positions [base, upto): re-base in place when
+  // nothing recorded at or after `base` must be kept, otherwise copy the kept
+  // columns into the other buffer.
   int reserve(int64_t base, int64_t upto) {
     const int G = (int)((ch.omega + 31) / 32);
     if (ch.bits && base >= ch.bits_base && upto - ch.bits_base <= ch.bits_cap) return PBN_OK;
     const int64_t keep_from = std::max(base, ch.bits_base);
-    const int64_t kept = ch.bits ? std::max<int64_t>(0, std::min(ch.length, ch.bits_base + ch.bits_cap) - keep_from) : 0;
+    const int64_t kept =
+        ch.bits ? std::max<int64_t>(0, std::min(ch.length, ch.bits_base + ch.bits_cap) - keep_from) : 0;
     int64_t cap = std::max<int64_t>(upto - base, 64);
     cap = std::max<int64_t>(cap, 2 * (ch.bits ? (ch.length - base) : 0));
     cap = (cap + 3) & ~int64_t(3);
-    uint32_t *nb = nullptr;
-    CUDA_TRY(cudaMallocAsync(&nb, sizeof(uint32_t) * (size_t)G * cap, s), "bitstream alloc");
-    if (ch.bits && kept > 0 && keep_from >= ch.bits_base) {
-      CUDA_TRY(cudaMemcpy2DAsync(nb + (keep_from - base), cap * 4, ch.bits + (keep_from - ch.bits_base), ch.bits_cap * 4,
-                                 kept * 4, G, cudaMemcpyDeviceToDevice, s),
+    int target = ws.cur_bits;
+    if (ch.bits && kept > 0) target ^= 1;   // copy source stays intact
+    int rc = ws.ensure(ws.bits[target], ws.bits_words[target], (size_t)G * cap, s, "bitstream alloc");
+    if (rc) return rc;
+    uint32_t *nb = ws.bits[target];
+    if (ch.bits && kept > 0) {
+      CUDA_TRY(cudaMemcpy2DAsync(nb + (keep_from - base), cap * 4, ch.bits + (keep_from - ch.bits_base),
+                                 ch.bits_cap * 4, kept * 4, G, cudaMemcpyDeviceToDevice, s),
                "bitstream copy");
     }
-    if (ch.bits) cudaFreeAsync(ch.bits, s);
+    ws.cur_bits = target;
     ch.bits = nb;
     ch.bits_cap = cap;
     ch.bits_base = base;
@@ -466,11 +524,9 @@ struct Query {
     int rc = reserve(keep_from, len);
     if (rc) return rc;
     const int64_t steps = len - ch.length;
-    cudaEvent_t a, b;
-    CUDA_TRY(cudaEventCreate(&a), "event");
-    CUDA_TRY(cudaEventCreate(&b), "event");
-    sim_ev.push_back(a);
-    sim_ev.push_back(b);
+    cudaEvent_t a = ws.event(n_events), b = ws.event(n_events + 1);
+    if (!a || !b) return fail(PBN_ERR_CUDA, "event creation failed");
+    n_events += 2;
     CUDA_TRY(cudaEventRecord(a, s), "event");
     rc = run_steps(net, cfg, ch, steps, s);
     if (rc) return rc;
@@ -489,20 +545,11 @@ struct Query {
 
   template <typename T>
   int fetch(T *h) {
-    CUDA_TRY(cudaMemcpyAsync(h_res, d_res, sizeof(T), cudaMemcpyDeviceToHost, s), "result copy");
+    CUDA_TRY(cudaMemcpyAsync(ws.h_res, d_res, sizeof(T), cudaMemcpyDeviceToHost, s), "result copy");
     CUDA_TRY(cudaStreamSynchronize(s), "stream sync");
-    memcpy(h, h_res, sizeof(T));
+    memcpy(h, ws.h_res, sizeof(T));
     d2h_bytes += sizeof(T);
     return PBN_OK;
-  }
-
-  double sim_ms() {
-    double total = 0.0;
-    for (size_t k = 0; k + 1 < sim_ev.size(); k += 2) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, sim_ev[k], sim_ev[k + 1]) == cudaSuccess) total += ms;
-    }
-    return total;
   }
 
   int gelman_rubin(int64_t psi0, double thr, int64_t max_length, int64_t *psi_out, double *rhat, int32_t *rounds) {
@@ -525,10 +572,19 @@ struct Query {
 
   double elapsed_ms() {
     float ms = 0.f;
-    cudaEventRecord(ev1, s);
-    cudaEventSynchronize(ev1);
-    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventRecord(ws.events[1], s);
+    cudaEventSynchronize(ws.events[1]);
+    cudaEventElapsedTime(&ms, ws.events[0], ws.events[1]);
     return ms;
+  }
+
+  double sim_ms() {
+    double total = 0.0;
+    for (size_t k = 2; k + 1 < n_events; k += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ws.events[k], ws.events[k + 1]) == cudaSuccess) total += ms;
+    }
+    return total;
   }
 };
 
