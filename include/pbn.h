@@ -280,6 +280,81 @@ typedef struct pbn_skart_report {
  * `stream`.  Errors as pbn_estimate_two_state. */
 int pbn_estimate_skart(const pbn_net *net, const pbn_skart_query *q, pbn_skart_report *out, void *stream);
 
+/* ------------------------------------------------- batched / served queries
+ *
+ * The engine advances many independent queries (each: a network, a state of
+ * interest, Alg. GR then Alg. 3 or Alg. 4 with its own seed and chain count)
+ * together.  Each epoch is one persistent simulation launch that extends
+ * every active query towards its next check, then one batched launch of the
+ * Gelman & Rubin / two-state statistics of the queries at a check (Skart
+ * checks run as their own launches after it).  The host then applies each
+ * query's stopping rule.  Chain states and bitstreams stay resident on the
+ * device from admission to completion.  Queries are admitted while a slot
+ * is free and the device-memory budget allows; a query's result is the same
+ * alone (pbn_estimate_two_state / pbn_estimate_skart) and in any mix,
+ * because its trajectory is a function of its own seed and its checks
+ * happen at the same lengths.  An autotuner picks transitions per epoch,
+ * threads per CTA and chain groups per CTA by timing live epochs.  The
+ * paper has no counterpart: this is the batching and serving layer. */
+
+enum { PBN_METHOD_TWO_STATE = 0, PBN_METHOD_SKART = 1 };
+#define PBN_ENGINE_MAX_ACTIVE 128
+
+typedef struct pbn_engine pbn_engine;
+
+typedef struct pbn_engine_cfg {
+    int64_t hbm_budget_bytes;   /* device bytes for chain states and bitstreams; 0 = 8 GiB */
+    int32_t max_active;         /* query slots, 1..PBN_ENGINE_MAX_ACTIVE; 0 = the maximum */
+    int32_t steps_per_epoch;    /* most transitions a query advances per epoch; 0 = autotuned */
+    int32_t threads_per_block;  /* 256 or 512; 0 = autotuned */
+    int32_t items_per_thread;   /* (node, chain group) items per thread when sizing CTAs; 0 = autotuned */
+    int32_t use_graph;          /* 1: each epoch is a captured CUDA graph, replayed */
+} pbn_engine_cfg;
+
+typedef struct pbn_engine_query {
+    const pbn_net *net;                /* must outlive the query */
+    int32_t method;                    /* PBN_METHOD_TWO_STATE or PBN_METHOD_SKART */
+    pbn_two_state_query two_state;     /* used for PBN_METHOD_TWO_STATE */
+    pbn_skart_query skart;             /* used for PBN_METHOD_SKART */
+    uint64_t tag;                      /* returned with the result */
+} pbn_engine_query;
+
+typedef struct pbn_engine_result {
+    int64_t id;
+    uint64_t tag;
+    int32_t method;
+    int32_t status;                    /* PBN_OK or the error that ended the query */
+    pbn_two_state_report two_state;
+    pbn_skart_report skart;
+    int64_t submit_epoch, admit_epoch, finish_epoch;
+} pbn_engine_result;
+
+typedef struct pbn_engine_stats {
+    int64_t epoch;
+    int32_t active, pending;
+    int64_t finished;                  /* results waiting to be polled */
+    int64_t updates;                   /* chain-node updates of this epoch */
+    double epoch_ms;                   /* device time of this epoch's launches */
+    int64_t hbm_in_use;
+    int32_t steps_per_epoch, threads_per_block, items_per_thread;
+    int32_t kernel_launches;           /* kernels this epoch launched */
+} pbn_engine_stats;
+
+/* Create an engine on the current device.  It runs on a stream of its own,
+ * ordered after the work already queued on `stream`, and allocates its fixed
+ * epoch buffers.  Errors: PBN_ERR_INVALID, PBN_ERR_OOM, PBN_ERR_CUDA. */
+int pbn_engine_create(const pbn_engine_cfg *cfg, void *stream, pbn_engine **out);
+void pbn_engine_destroy(pbn_engine *engine);
+/* Queue a query (host arguments copied).  *id identifies its result.
+ * Errors: PBN_ERR_INVALID (as the single-query drivers). */
+int pbn_engine_submit(pbn_engine *engine, const pbn_engine_query *query, int64_t *id);
+/* One epoch: admit, simulate, check, retire.  Synchronises the stream.
+ * A query that fails ends with its status in the result; the call itself
+ * fails only for engine-wide errors (PBN_ERR_CUDA, PBN_ERR_OOM). */
+int pbn_engine_step(pbn_engine *engine, pbn_engine_stats *stats);
+/* Move up to max_results finished results into out (host memory). */
+int pbn_engine_poll(pbn_engine *engine, pbn_engine_result *out, int32_t max_results, int32_t *count);
+
 /* ---------------------------------------------------------------- errors */
 
 const char *pbn_last_error(void);

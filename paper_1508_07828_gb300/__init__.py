@@ -112,6 +112,29 @@ class SkartReport(ctypes.Structure):
                 ("kernel_launches", c_i64), ("sim_items", c_i64), ("d2h_bytes", c_i64)]
 
 
+class EngineCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", c_i64), ("max_active", c_i32), ("steps_per_epoch", c_i32),
+                ("threads_per_block", c_i32), ("items_per_thread", c_i32), ("use_graph", c_i32)]
+
+
+class EngineQuery(ctypes.Structure):
+    _fields_ = [("net", c_vp), ("method", c_i32), ("two_state", TwoStateQuery), ("skart", SkartQuery), ("tag", c_u64)]
+
+
+class EngineResult(ctypes.Structure):
+    _fields_ = [("id", c_i64), ("tag", c_u64), ("method", c_i32), ("status", c_i32), ("two_state", TwoStateReport),
+                ("skart", SkartReport), ("submit_epoch", c_i64), ("admit_epoch", c_i64), ("finish_epoch", c_i64)]
+
+
+class EngineStats(ctypes.Structure):
+    _fields_ = [("epoch", c_i64), ("active", c_i32), ("pending", c_i32), ("finished", c_i64), ("updates", c_i64),
+                ("epoch_ms", c_dbl), ("hbm_in_use", c_i64), ("steps_per_epoch", c_i32),
+                ("threads_per_block", c_i32), ("items_per_thread", c_i32), ("kernel_launches", c_i32)]
+
+
+METHOD_TWO_STATE = 0
+METHOD_SKART = 1
+
 _lock = threading.Lock()
 _lib = None
 
@@ -138,6 +161,12 @@ def lib():
             L.pbn_skart_static.argtypes = [P(Chains), c_i64, c_i64, c_i64, c_i64, c_dbl, c_dbl, c_vp, c_vp]
             L.pbn_estimate_two_state.argtypes = [c_vp, P(TwoStateQuery), P(TwoStateReport), c_vp]
             L.pbn_estimate_skart.argtypes = [c_vp, P(SkartQuery), P(SkartReport), c_vp]
+            L.pbn_engine_create.argtypes = [P(EngineCfg), c_vp, P(c_vp)]
+            L.pbn_engine_destroy.argtypes = [c_vp]
+            L.pbn_engine_destroy.restype = None
+            L.pbn_engine_submit.argtypes = [c_vp, P(EngineQuery), P(c_i64)]
+            L.pbn_engine_step.argtypes = [c_vp, P(EngineStats)]
+            L.pbn_engine_poll.argtypes = [c_vp, c_vp, c_i32, P(c_i32)]
             L.pbn_last_error.restype = ctypes.c_char_p
             L.pbn_status_string.restype = ctypes.c_char_p
             L.pbn_status_string.argtypes = [ctypes.c_int]
@@ -367,3 +396,96 @@ def pbn_estimate_skart(network: Network, soi, omega: int, seed: int, H_star: flo
     out = SkartReport()
     _check(lib().pbn_estimate_skart(network.handle, ctypes.byref(q), ctypes.byref(out), _stream(stream)))
     return _as_struct(SkartReport, out)
+
+
+# ------------------------------------------------------------------ engine
+
+def _report(cls, obj):
+    return _as_struct(cls, obj)
+
+
+class Engine:
+    """Batched / served queries (pbn_engine_* in include/pbn.h): queries of
+    uneven size advance together, one persistent simulation launch and one
+    batched statistics launch per epoch, admitted as slots and the
+    device-memory budget allow."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_active: int = 0, steps_per_epoch: int = 0,
+                 threads_per_block: int = 0, items_per_thread: int = 0, use_graph: bool = True, stream=None):
+        cfg = EngineCfg(int(hbm_budget_bytes), int(max_active), int(steps_per_epoch), int(threads_per_block),
+                        int(items_per_thread), int(bool(use_graph)))
+        h = c_vp()
+        _check(lib().pbn_engine_create(ctypes.byref(cfg), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self._nets = {}
+
+    def submit_two_state(self, network: Network, soi, omega: int, seed: int, psi0: int = 1024, rhat: float = 1.05,
+                         eps: float = 1e-10, r: float = 0.005, s: float = 0.95, mode: int = PER_NODE,
+                         max_length: int = 1 << 26, tag: int = 0) -> int:
+        soi_arg = SoiArg(soi)
+        q = EngineQuery()
+        q.net = network.handle
+        q.method = METHOD_TWO_STATE
+        q.two_state = TwoStateQuery(int(omega), int(psi0), float(rhat), float(eps), float(r), float(s),
+                                    int(max_length), int(seed), int(mode), soi_arg.struct)
+        q.tag = int(tag)
+        qid = c_i64()
+        _check(lib().pbn_engine_submit(self.handle, ctypes.byref(q), ctypes.byref(qid)))
+        self._nets[qid.value] = network
+        return qid.value
+
+    def submit_skart(self, network: Network, soi, omega: int, seed: int, H_star: float, relative: bool = True,
+                     alpha: float = 0.05, psi0: int = 1024, rhat: float = 1.05, mode: int = PER_NODE,
+                     max_length: int = 1 << 26, tag: int = 0) -> int:
+        soi_arg = SoiArg(soi)
+        q = EngineQuery()
+        q.net = network.handle
+        q.method = METHOD_SKART
+        q.skart = SkartQuery(int(omega), int(psi0), float(rhat), float(H_star), int(bool(relative)), float(alpha),
+                             int(max_length), int(seed), int(mode), soi_arg.struct)
+        q.tag = int(tag)
+        qid = c_i64()
+        _check(lib().pbn_engine_submit(self.handle, ctypes.byref(q), ctypes.byref(qid)))
+        self._nets[qid.value] = network
+        return qid.value
+
+    def step(self) -> dict:
+        st = EngineStats()
+        _check(lib().pbn_engine_step(self.handle, ctypes.byref(st)))
+        return _as_struct(EngineStats, st)
+
+    def poll(self, max_results: int = 256) -> list:
+        buf = (EngineResult * max_results)()
+        n = c_i32()
+        _check(lib().pbn_engine_poll(self.handle, ctypes.cast(buf, c_vp), int(max_results), ctypes.byref(n)))
+        out = []
+        for k in range(n.value):
+            r = buf[k]
+            d = {"id": r.id, "tag": r.tag, "method": r.method, "status": r.status,
+                 "submit_epoch": r.submit_epoch, "admit_epoch": r.admit_epoch, "finish_epoch": r.finish_epoch}
+            d["report"] = _as_struct(TwoStateReport if r.method == METHOD_TWO_STATE else SkartReport,
+                                     r.two_state if r.method == METHOD_TWO_STATE else r.skart)
+            self._nets.pop(r.id, None)
+            out.append(d)
+        return out
+
+    def run(self, max_epochs: int = 1_000_000) -> list:
+        """Step until nothing is active or waiting; returns all results."""
+        results = []
+        for _ in range(max_epochs):
+            st = self.step()
+            results += self.poll()
+            if st["active"] == 0 and st["pending"] == 0:
+                break
+        return results
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pbn_engine_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -17,8 +17,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpbn_gb300.so")
 
-SOURCES = ["pbn_sim.cu", "pbn_stats.cu", "pbn_api.cu", "pbn_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "pbn_internal.cuh"), os.path.join(INCLUDE, "pbn.h")]
+SOURCES = ["pbn_sim.cu", "pbn_stats.cu", "pbn_api.cu", "pbn_noalloc.cu", "pbn_engine.cu"]
+HEADERS = [os.path.join(CSRC, "pbn_internal.cuh"), os.path.join(CSRC, "pbn_step.cuh"),
+           os.path.join(CSRC, "pbn_stats.cuh"),
+           os.path.join(INCLUDE, "pbn.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +34,8 @@ def nvcc() -> str:
 def _flags(src: str, verbose_ptxas: bool):
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
                 "-I", INCLUDE, "-I", CSRC]
-    if src == "pbn_stats.cu":
+    if src in ("pbn_stats.cu", "pbn_engine.cu"):
+        # FP64 statistics round as in plain C (no fused multiply-add)
         f += ["--fmad=false"]
     if verbose_ptxas:
         f += ["-Xptxas", "-v"]

@@ -14,10 +14,6 @@
 
 #include "pbn_internal.cuh"
 
-struct pbn_net {
-  pbn::NetDev dev;
-  int device = 0;
-};
 
 namespace {
 

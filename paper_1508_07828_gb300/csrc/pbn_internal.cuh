@@ -85,7 +85,9 @@ struct SimArgs {
   int soi_size;
   uint16_t soi_node[kMaxSoi];
   uint32_t soi_val;      // bit m = required value of soi_node[m]
+  int mode;              // perturbation reading (batched kernel only)
 };
+static_assert(sizeof(SimArgs) % 4 == 0, "SimArgs is copied word by word");
 
 // Sets the thread-local message returned by pbn_last_error (pbn_api.cu).
 void set_last_error(const char *msg);
@@ -124,3 +126,9 @@ cudaError_t launch_skart_into(const pbn_chains &ch, int64_t col, int64_t kappa, 
                               cudaStream_t s);
 
 }  // namespace pbn
+
+// The library-owned network handle of the C ABI.
+struct pbn_net {
+  pbn::NetDev dev;
+  int device = 0;
+};

@@ -1,0 +1,315 @@
+// Device code of the synchronous PBN step shared by the single-task and the
+// batched simulation kernels (see pbn_sim.cu for the method).
+#pragma once
+
+#include "pbn_internal.cuh"
+
+namespace pbn {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t sext_bit(uint32_t w, int b) {
+  return (uint32_t)((int32_t)(w << (31 - b)) >> 31);
+}
+
+// Multiplexer-tree evaluation of a K-input truth table on bit-sliced inputs:
+// leaf j = truth-table bit j (as 0 or ~0); level m selects on x[m].
+template <int K>
+__device__ __forceinline__ uint32_t eval_tt(uint32_t tt, const uint32_t *x) {
+  if constexpr (K == 0) {
+    return sext_bit(tt, 0);
+  } else {
+    constexpr int NL = 1 << K;
+    uint32_t v[NL / 2];
+#pragma unroll
+    for (int q = 0; q < NL / 2; q++) {
+      const uint32_t lo = sext_bit(tt, 2 * q), hi = sext_bit(tt, 2 * q + 1);
+      v[q] = (x[0] & hi) | (~x[0] & lo);
+    }
+#pragma unroll
+    for (int m = 1; m < K; m++) {
+#pragma unroll
+      for (int q = 0; q < (NL >> (m + 1)); q++) v[q] = (x[m] & v[2 * q + 1]) | (~x[m] & v[2 * q]);
+    }
+    return v[0];
+  }
+}
+
+// Function record evaluated at tree depth K >= its own k: the truth table is
+// replicated to 2^K leaves; parents m >= k are node 0 (their value then does
+// not matter).
+template <int K>
+__device__ __forceinline__ uint32_t eval_at_depth(uint4 rec, int k, const uint32_t *cur, int gpb, int gl) {
+  uint32_t tt = rec.x;
+#pragma unroll
+  for (int e = 0; e < K; e++)
+    if (e >= k) tt |= tt << (1 << e);
+  int p[5];
+  p[0] = rec.z & 0xFFF;
+  p[1] = (rec.z >> 12) & 0xFFF;
+  p[2] = rec.w & 0xFFF;
+  p[3] = (rec.w >> 12) & 0xFFF;
+  p[4] = (int)((rec.z >> 24) | (((rec.w >> 24) & 0xFu) << 8));
+  uint32_t x[5];
+#pragma unroll
+  for (int m = 0; m < K; m++) x[m] = cur[p[m] * gpb + gl];
+  return eval_tt<K>(tt, x);
+}
+
+// K is warp-uniform, so the switch does not diverge.
+__device__ __forceinline__ uint32_t eval_uniform(int K, uint4 rec, int k, const uint32_t *cur, int gpb, int gl) {
+  switch (K) {
+    case 0: return eval_at_depth<0>(rec, k, cur, gpb, gl);
+    case 1: return eval_at_depth<1>(rec, k, cur, gpb, gl);
+    case 2: return eval_at_depth<2>(rec, k, cur, gpb, gl);
+    case 3: return eval_at_depth<3>(rec, k, cur, gpb, gl);
+    case 4: return eval_at_depth<4>(rec, k, cur, gpb, gl);
+    default: return eval_at_depth<5>(rec, k, cur, gpb, gl);
+  }
+}
+
+struct ItemCtx {
+  const uint4 *fn_s;
+  const uint32_t *cur;
+  uint32_t *nxt;
+  uint32_t *pbuf;
+  unsigned int *anyP;
+  bool active;
+  int i, L, f0;
+  uint32_t g;
+  int gl, gpb;
+  uint32_t vmask;
+  uint64_t t;
+  int sub;
+};
+
+// One item of one transition with LW (warp-uniform) category bounds; bound 0
+// is P32, bound m is T_{m-1}; bounds m >= L are unreachable (all lanes below).
+template <int LW, int MODE, int T, int BPR>
+__device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
+  uint32_t ts[LW], und[LW], lt[LW];
+#pragma unroll
+  for (int m = 0; m < LW; m++) {
+    const bool real = m < c.L;
+    ts[m] = (m == 0) ? P32 : (real ? c.fn_s[c.f0 + m - 1].y : 0u);
+    und[m] = real ? c.vmask : 0u;
+    lt[m] = real ? 0u : kFull;
+  }
+  const uint32_t cy = (uint32_t)c.t, cz = (uint32_t)(c.t >> 32) & 0xFFFFFFu;
+#pragma unroll 1
+  for (int round = 0; round * T * BPR < 8; round++) {
+    uint32_t pend = 0u;
+#pragma unroll
+    for (int m = 0; m < LW; m++) pend |= und[m];
+    if (!__any_sync(kFull, pend != 0u)) break;
+    uint32_t u[LW], l[LW];
+#pragma unroll
+    for (int m = 0; m < LW; m++) {
+      u[m] = kFull;
+      l[m] = 0u;
+    }
+#pragma unroll
+    for (int cblk = 0; cblk < BPR; cblk++) {
+      const uint32_t b = (uint32_t)((round * T + c.sub) * BPR + cblk);
+      const uint4 R = philox4x32_10(make_uint4((uint32_t)c.i, cy, cz | (b << 24), c.g), rk);
+      const uint32_t Rq[4] = {R.x, R.y, R.z, R.w};
+#pragma unroll
+      for (int m = 0; m < LW; m++) {
+        const uint32_t tsb = ts[m] << (4u * b);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          // bound digit as 0 / ~0; lanes whose digit differs are decided
+          const uint32_t tm = (uint32_t)((int32_t)(tsb << q) >> 31);
+          const uint32_t dec = u[m] & (Rq[q] ^ tm);
+          l[m] |= dec & tm;  // bound digit 1, lane digit 0: u < bound
+          u[m] &= ~dec;
+        }
+      }
+    }
+    // merge the T threads' consecutive digit blocks in order
+#pragma unroll
+    for (int k = 1; k < T; k <<= 1) {
+#pragma unroll
+      for (int m = 0; m < LW; m++) {
+        const uint32_t pu = __shfl_xor_sync(kFull, u[m], k);
+        const uint32_t pl = __shfl_xor_sync(kFull, l[m], k);
+        if (c.sub & k) {
+          l[m] = pl | (pu & l[m]);
+        } else {
+          l[m] = l[m] | (u[m] & pl);
+        }
+        u[m] &= pu;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < LW; m++) {
+      lt[m] |= und[m] & l[m];
+      und[m] &= u[m];
+    }
+  }
+  // lanes of function j: below bound j+1 and not below bound j
+  uint32_t sel[LW];
+  {
+    uint32_t prev = lt[0];
+#pragma unroll
+    for (int j = 0; j < LW; j++) {
+      const uint32_t upto = (j + 1 < LW) ? lt[j + 1] : kFull;
+      sel[j] = upto & ~prev & c.vmask;
+      prev = upto;
+    }
+  }
+  uint32_t fword = 0u;
+#pragma unroll
+  for (int p0 = 0; p0 < LW; p0 += T) {
+    uint32_t my_sel = 0u;
+#pragma unroll
+    for (int s = 0; s < T; s++)
+      if (s == c.sub && p0 + s < LW) my_sel = sel[p0 + s];
+    const int j = p0 + c.sub;
+    const bool has = (j < c.L) && my_sel != 0u;
+    const uint4 rec = has ? c.fn_s[c.f0 + j] : make_uint4(0u, 0u, 0u, 0u);
+    const int k = has ? fn_k(rec) : 0;
+    const int K = __reduce_max_sync(kFull, (unsigned)k);
+    if (__any_sync(kFull, has)) fword |= my_sel & eval_uniform(K, rec, k, c.cur, c.gpb, c.gl);
+  }
+#pragma unroll
+  for (int k = 1; k < T; k <<= 1) fword |= __shfl_xor_sync(kFull, fword, k);
+  if (c.active && c.sub == 0) {
+    const int idx = c.i * c.gpb + c.gl;
+    if (MODE == PBN_PERTURB_PER_NODE) {
+      c.nxt[idx] = (lt[0] & ~c.cur[idx]) | fword;
+    } else {
+      c.nxt[idx] = fword;
+      c.pbuf[idx] = lt[0];
+      if (lt[0]) atomicOr(&c.anyP[c.gl], lt[0]);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t lane_mask(int64_t omega, uint32_t g) {
+  int64_t rem = omega - (int64_t)g * 32;
+  return rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
+}
+
+// Nodes with more than 4 functions are rare; their variant is kept out of
+// line so its register demand does not raise the common path's.
+template <int MODE, int T, int BPR>
+__device__ __noinline__ void step_item_wide(const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
+  step_item<kMaxL, MODE, T, BPR>(rk, P32, c);
+}
+
+template <int MODE, int T, int BPR>
+__device__ __forceinline__ void dispatch_item(int LW, const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
+  switch (LW) {
+    case 0: break;
+    case 1: step_item<1, MODE, T, BPR>(rk, P32, c); break;
+    case 2: step_item<2, MODE, T, BPR>(rk, P32, c); break;
+    case 3: step_item<3, MODE, T, BPR>(rk, P32, c); break;
+    case 4: step_item<4, MODE, T, BPR>(rk, P32, c); break;
+    default: step_item_wide<MODE, T, BPR>(rk, P32, c); break;
+  }
+}
+
+// Threads per CTA a variant is compiled for: one thread per item may fill
+// 1024 threads (64 registers each); shared items run at most 512 threads.
+template <int T>
+constexpr int max_threads() { return T == 1 ? 1024 : 512; }
+
+// One CTA's work: advance chain groups g0 .. g0+ngl-1 of task `a` by
+// a.steps transitions.  `rk` are the task's Philox round keys (kernel
+// parameters in the single-task kernel, registers in the batched one).
+template <int MODE, int T, int BPR>
+__device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &rk, uint32_t g0, int ngl,
+                                             unsigned char *smem) {
+  const int gpb = a.gpb;
+  const int n = a.n;
+  const uint32_t P32 = a.P32;
+  const uint4 *fn_s = a.fn;
+  const uint32_t *node_s = a.node;
+  size_t off = 0;
+  if (a.tables_in_smem) {
+    uint4 *f = reinterpret_cast<uint4 *>(smem);
+    for (int j = threadIdx.x; j < a.F; j += blockDim.x) f[j] = a.fn[j];
+    off = (size_t)a.F * 16;
+    uint32_t *nd = reinterpret_cast<uint32_t *>(smem + off);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) nd[j] = a.node[j];
+    off += ((size_t)n * 4 + 15) & ~(size_t)15;
+    fn_s = f;
+    node_s = nd;
+  }
+  const int items = n * gpb;
+  uint32_t *bufA = reinterpret_cast<uint32_t *>(smem + off);
+  uint32_t *bufB = bufA + items;
+  uint32_t *pbuf = bufB + items;
+  unsigned int *anyP = reinterpret_cast<unsigned int *>(pbuf + items);  // [2][gpb]
+  for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+    int i = idx / gpb, gl = idx - i * gpb;
+    bufA[idx] = gl < ngl ? a.state[(size_t)(g0 + gl) * n + i] : 0u;
+  }
+  if (MODE == PBN_PERTURB_GLOBAL)
+    for (int j = threadIdx.x; j < 2 * gpb; j += blockDim.x) anyP[j] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int sub = lane & (T - 1);
+  const int slot = threadIdx.x / T;
+  const int nslots = blockDim.x / T;
+  uint32_t *cur = bufA, *nxt = bufB;
+  for (int s = 0; s < a.steps; s++) {
+    ItemCtx c;
+    c.fn_s = fn_s;
+    c.cur = cur;
+    c.nxt = nxt;
+    c.pbuf = pbuf;
+    c.anyP = anyP + (s & 1) * gpb;
+    c.gpb = gpb;
+    c.t = a.t0 + (uint64_t)s;
+    c.sub = sub;
+    for (int base = 0; base < items; base += nslots) {  // uniform trip count
+      const int q = base + slot;
+      const int r = q / gpb;
+      c.gl = q - r * gpb;
+      c.active = (q < items) && (c.gl < ngl);
+      const uint32_t rec = c.active ? node_s[r] : 0u;
+      c.L = c.active ? node_l(rec) : 0;
+      c.i = node_id(rec);
+      c.f0 = node_f0(rec);
+      c.g = g0 + (uint32_t)c.gl;
+      c.vmask = c.active ? lane_mask(a.omega, c.g) : 0u;
+      const int LW = (int)__reduce_max_sync(kFull, (unsigned)c.L);
+      dispatch_item<MODE, T, BPR>(LW, rk, P32, c);
+    }
+    __syncthreads();
+    if (MODE == PBN_PERTURB_GLOBAL) {
+      for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const uint32_t any = c.anyP[idx % gpb];
+        nxt[idx] = (any & (cur[idx] ^ pbuf[idx])) | (~any & nxt[idx]);
+      }
+      unsigned int *anyN = anyP + ((s + 1) & 1) * gpb;
+      for (int j = threadIdx.x; j < gpb; j += blockDim.x) anyN[j] = 0u;
+      __syncthreads();
+    }
+    if (a.soi_size > 0) {
+      const int64_t col = a.col0 + s;
+      for (int gl = warp; gl < ngl; gl += nwarps) {
+        uint32_t v = kFull;
+        if (lane < a.soi_size) {
+          const uint32_t w = nxt[a.soi_node[lane] * gpb + gl];
+          v = ((a.soi_val >> lane) & 1u) ? w : ~w;
+        }
+        v = __reduce_and_sync(kFull, v);
+        if (lane == 0 && col >= 0) a.bits[(size_t)(g0 + gl) * a.bits_cap + col] = v & lane_mask(a.omega, g0 + gl);
+      }
+    }
+    uint32_t *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+    int i = idx / gpb, gl = idx - i * gpb;
+    if (gl < ngl) a.state[(size_t)(g0 + gl) * n + i] = cur[idx];
+  }
+}
+
+
+}  // namespace pbn

@@ -69,6 +69,14 @@ STRUCTS = {
                                          "length", "kappa", "batches", "spacer", "sample_size", "gr_rounds",
                                          "rand_rounds", "ci_rounds", "chain_node_updates", "device_ms", "sim_ms",
                                          "sim_launches", "kernel_launches", "sim_items", "d2h_bytes"]),
+    "EngineCfg": ("pbn_engine_cfg", ["hbm_budget_bytes", "max_active", "steps_per_epoch", "threads_per_block",
+                                     "items_per_thread", "use_graph"]),
+    "EngineQuery": ("pbn_engine_query", ["net", "method", "two_state", "skart", "tag"]),
+    "EngineResult": ("pbn_engine_result", ["id", "tag", "method", "status", "two_state", "skart", "submit_epoch",
+                                           "admit_epoch", "finish_epoch"]),
+    "EngineStats": ("pbn_engine_stats", ["epoch", "active", "pending", "finished", "updates", "epoch_ms",
+                                         "hbm_in_use", "steps_per_epoch", "threads_per_block", "items_per_thread",
+                                         "kernel_launches"]),
 }
 
 
