@@ -55,6 +55,12 @@ def parse():
     ap.add_argument("--threads-per-item", type=int, default=0)
     ap.add_argument("--blocks-per-round", type=int, default=0)
     ap.add_argument("--groups-per-block", type=int, default=0)
+    ap.add_argument("--batched", action="store_true",
+                    help="64 networks of uneven size: the engine vs the plain one-query-at-a-time loop")
+    ap.add_argument("--serve", action="store_true", help="Poisson arrivals over a pool of 200 networks")
+    ap.add_argument("--rates", default="50,200,1000,2000", help="arrival rates (queries/s) for --serve")
+    ap.add_argument("--queries", type=int, default=120, help="queries per rate for --serve")
+    ap.add_argument("--max-length", type=int, default=1 << 20)
     return ap.parse_args()
 
 
@@ -401,10 +407,159 @@ def run_sim_only(args):
                       "launch": launch}))
 
 
+def _percentiles(x):
+    x = np.asarray(x, dtype=np.float64)
+    return {"p50": float(np.percentile(x, 50)), "p99": float(np.percentile(x, 99)), "mean": float(x.mean())}
+
+
+def run_batched(args):
+    """64 independent networks (n log-uniform in [50, 3000], 256-4096
+    chains, p in {0.001, 0.01}, two-state at r = 0.005): the engine (one
+    persistent launch per epoch, CUDA graph, autotuned) against the plain
+    loop of one pbn_estimate_two_state per network, same seeds."""
+    import torch
+    import pbn_synth as S
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+    torch.cuda.set_device(0)
+    cfgs = S.batch_configs()
+    nets = [P.pbn_load(net) for net, _, _ in cfgs]
+    kw = lambda c, k: dict(omega=c["omega"], seed=1000 + k, psi0=PSI0, rhat=c["rhat"], eps=c["eps"], r=c["r"],
+                           s=c["s"], max_length=args.max_length)
+
+    def plain():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat, upd, ok = [], 0, 0
+        for k, ((net, soi, c), N) in enumerate(zip(cfgs, nets)):
+            try:
+                r = P.pbn_estimate_two_state(N, soi, **kw(c, k))
+                upd += r["chain_node_updates"]
+                ok += 1
+            except P.PbnError:
+                pass
+            lat.append(time.perf_counter() - t0)
+        return time.perf_counter() - t0, upd, ok, lat
+
+    def batched():
+        eng = P.Engine(use_graph=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k, ((net, soi, c), N) in enumerate(zip(cfgs, nets)):
+            eng.submit_two_state(N, soi, tag=k, **kw(c, k))
+        upd, ok, lat, epochs, ms = 0, 0, [], 0, 0.0
+        while True:
+            st = eng.step()
+            epochs += 1
+            ms += st["epoch_ms"]
+            for r in eng.poll():
+                lat.append(time.perf_counter() - t0)
+                upd += r["report"]["chain_node_updates"]
+                ok += r["status"] == 0
+            if st["active"] == 0 and st["pending"] == 0:
+                break
+        wall = time.perf_counter() - t0
+        eng.close()
+        return wall, upd, ok, lat, epochs, st
+
+    # warm-up runs let the engine's autotuner settle (its choice persists
+    # for later engines of the process)
+    for _ in range(max(1, args.warmup)):
+        batched()
+    plain()
+    pw, pu, pok, plat = plain()
+    bw, bu, bok, blat, epochs, st = batched()
+    print(json.dumps({"mode": "batched", "networks": len(cfgs), "config": "64 nets, n log-uniform [50,3000], "
+                      "chains log-uniform [256,4096], p in {0.001,0.01}, two-state r=0.005",
+                      "plain": {"seconds": pw, "updates_per_s": pu / pw, "queries_ok": pok,
+                                "latency_s": _percentiles(plat)},
+                      "batched": {"seconds": bw, "updates_per_s": bu / bw, "queries_ok": bok, "epochs": epochs,
+                                  "latency_s": _percentiles(blat),
+                                  "tuned": {k: st[k] for k in ("steps_per_epoch", "threads_per_block",
+                                                               "items_per_thread")}},
+                      "speedup": pw / bw, "same_updates": pu == bu}))
+
+
+def run_serve(args):
+    """Serving: queries arrive as a Poisson process; each names a random
+    network of the 200-network pool (n log-uniform in [20, 3000]), a state
+    of interest of 1-10 nodes and r in {0.01, 0.005, 0.001} (two-state, 1024
+    chains).  The engine admits them while others run (continuous batching);
+    the baseline serves the same arrival trace one query at a time."""
+    import torch
+    import pbn_synth as S
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+    torch.cuda.set_device(0)
+    pool = S.serving_pool()
+    nets = [P.pbn_load(n) for n in pool]
+    rng = np.random.default_rng(1508078284)
+    out = {"mode": "serve", "pool": len(pool), "queries_per_rate": args.queries, "rates": []}
+    for rate in [float(x) for x in args.rates.split(",")]:
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.queries))
+        qs = []
+        for k in range(args.queries):
+            i = int(rng.integers(len(pool)))
+            qs.append((i, S.random_soi(rng, pool[i].n), float(rng.choice([0.01, 0.005, 0.001])), 10_000 + k))
+        # engine, continuous batching
+        eng = P.Engine(use_graph=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nxt, lat, upd, done, ok = 0, [], 0, 0, 0
+        while done < len(qs):
+            now = time.perf_counter() - t0
+            while nxt < len(qs) and arrivals[nxt] <= now:
+                i, soi, r, seed = qs[nxt]
+                eng.submit_two_state(nets[i], soi, omega=1024, seed=seed, psi0=PSI0, rhat=1.05, r=r,
+                                     max_length=args.max_length, tag=nxt)
+                nxt += 1
+            st = eng.step()
+            for res in eng.poll():
+                lat.append(time.perf_counter() - t0 - arrivals[res["tag"]])
+                upd += res["report"]["chain_node_updates"]
+                ok += res["status"] == 0
+                done += 1
+            if st["active"] == 0 and st["pending"] == 0 and nxt < len(qs):
+                time.sleep(max(0.0, min(0.001, arrivals[nxt] - (time.perf_counter() - t0))))
+        wall = time.perf_counter() - t0
+        eng.close()
+        # baseline: the same trace served one query at a time
+        t0 = time.perf_counter()
+        blat, bupd, free_at = [], 0, 0.0
+        for k, (i, soi, r, seed) in enumerate(qs):
+            start = max(free_at, arrivals[k])
+            wait = start - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            try:
+                rep = P.pbn_estimate_two_state(nets[i], soi, omega=1024, seed=seed, psi0=PSI0, rhat=1.05, r=r,
+                                               max_length=args.max_length)
+                bupd += rep["chain_node_updates"]
+            except P.PbnError:
+                pass
+            free_at = time.perf_counter() - t0
+            blat.append(free_at - arrivals[k])
+        bwall = time.perf_counter() - t0
+        out["rates"].append({"rate_per_s": rate,
+                             "engine": {"latency_s": _percentiles(lat), "queries_per_s": len(qs) / wall,
+                                        "updates_per_s": upd / wall, "ok": ok},
+                             "one_at_a_time": {"latency_s": _percentiles(blat), "queries_per_s": len(qs) / bwall,
+                                               "updates_per_s": bupd / bwall}})
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.sim_only:
         run_sim_only(args)
+        return
+    if args.batched:
+        run_batched(args)
+        return
+    if args.serve:
+        run_serve(args)
         return
     if args.impl == "reference":
         run_reference(args)

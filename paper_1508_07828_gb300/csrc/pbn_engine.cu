@@ -33,6 +33,7 @@
 #include <algorithm>
 #include <deque>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "pbn_stats.cuh"
@@ -307,6 +308,12 @@ namespace {
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// The autotuner's last choice in this process: later engines without fixed
+// settings start from it instead of tuning again.
+std::mutex g_tuned_mu;
+bool g_tuned = false;
+Candidate g_tuned_cand;
+
 // Dynamic shared memory one batched-simulation CTA may use: the opt-in
 // maximum less the kernel's own static shared memory.
 int smem_limit() {
@@ -320,11 +327,14 @@ int smem_limit() {
   return v;
 }
 
-// Chain groups per CTA for one query: about threads * ipt items, within the
+// Chain groups per CTA for one query: about threads * ipt items, at most
+// gpb_cap (so that a light epoch still spreads over the SMs), within the
 // shared memory one CTA may use.
-void size_task(const EQuery &q, int threads, int ipt, size_t smem_cap, int *gpb_out, bool *tables_out) {
+void size_task(const EQuery &q, int threads, int ipt, int gpb_cap, size_t smem_cap, int *gpb_out,
+               bool *tables_out) {
   const NetDev &d = q.dev();
   int gpb = std::max(1, threads * ipt / std::max(1, d.n));
+  gpb = std::min(gpb, std::max(1, gpb_cap));
   gpb = std::min(gpb, q.G);
   for (;;) {
     if (sim_smem_bytes(d.n, d.F, gpb, q.mode, true) <= smem_cap) { *tables_out = true; break; }
@@ -646,7 +656,7 @@ extern "C" int pbn_engine_create(const pbn_engine_cfg *cfg, void *stream, pbn_en
   memset(e->h_cnt, 0, sizeof(int) * kCounters);
   ECUDA(cudaFuncSetAttribute(batch_sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit()), "smem attr");
   // candidates of the autotuner (a fixed setting leaves one candidate)
-  const int Ss[] = {512, 2048, 8192};
+  const int Ss[] = {1024, 4096};
   const int Ts[] = {256, 512};
   const int Is[] = {2, 8};
   for (int S : Ss)
@@ -662,6 +672,13 @@ extern "C" int pbn_engine_create(const pbn_engine_cfg *cfg, void *stream, pbn_en
         e->cands.push_back(cd);
       }
   if (e->cands.size() == 1) e->best = 0;
+  if (e->best < 0) {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    if (g_tuned) {
+      e->cands.assign(1, g_tuned_cand);
+      e->best = 0;
+    }
+  }
   *out = e.release();
   return PBN_OK;
 }
@@ -740,6 +757,12 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
   if (ci < 0) ci = e->round_robin++ % (int)e->cands.size();
   const Candidate &cand = e->cands[ci];
   size_t smem_cap = (size_t)smem_limit();
+  // spread light epochs: at least about two CTAs per SM when the active
+  // chain groups allow it
+  int64_t total_groups = 0;
+  for (auto &qp : e->active)
+    if (qp->phase != PH_DONE && qp->ch.length < qp->target) total_groups += qp->G;
+  const int gpb_cap = (int)std::max<int64_t>(1, total_groups / (2 * (int64_t)e->sms));
   int ntask = 0, nitems = 0, nreq = 0, vblocks = 0;
   size_t smem = 0;
   int64_t updates = 0;
@@ -757,7 +780,7 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       if ((rc = reserve_bits(e, q, q.keep_from, q.ch.length + D))) { finish(e, q, rc); continue; }
       int gpb;
       bool tables;
-      size_task(q, cand.threads, cand.ipt, smem_cap, &gpb, &tables);
+      size_task(q, cand.threads, cand.ipt, gpb_cap, smem_cap, &gpb, &tables);
       const int64_t groups_items = cdiv(q.G, gpb);
       if (nitems + groups_items > e->max_items) continue;   // next epoch
       SimArgs &a = e->h_tasks[ntask];
@@ -876,13 +899,16 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
     c.updates += updates;
     c.trials++;
     bool all = true;
-    for (auto &x : e->cands) all = all && x.trials >= 2;
+    for (auto &x : e->cands) all = all && x.trials >= 1;
     if (all) {
       double bestv = -1;
       for (size_t k = 0; k < e->cands.size(); k++) {
         const double v = e->cands[k].updates / std::max(1e-9, e->cands[k].ms);
         if (v > bestv) { bestv = v; e->best = (int)k; }
       }
+      std::lock_guard<std::mutex> lk(g_tuned_mu);
+      g_tuned = true;
+      g_tuned_cand = e->cands[e->best];
     }
   }
   retire(e);
