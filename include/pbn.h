@@ -116,6 +116,8 @@ typedef struct pbn_run_cfg {
     int32_t threads_per_block;  /* 0 = automatic */
     int32_t threads_per_item;   /* threads sharing one (node, chain group) update: 1, 2, 4; 0 = automatic */
     int32_t blocks_per_round;   /* Philox blocks per thread per round when threads_per_item = 1: 1, 2; 0 = auto */
+    int32_t staging;            /* function records: 0 = automatic (shared memory if they fit, else TMA
+                                   tiles), 1 = whole tables in shared memory, 2 = TMA tiles, 3 = global */
 } pbn_run_cfg;
 
 /* ---------------------------------------------------------------- network */
@@ -144,6 +146,15 @@ int pbn_init_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *chai
  * Errors: PBN_ERR_INVALID (SOI, capacity), PBN_ERR_CUDA. */
 int pbn_run_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *chains, int64_t steps,
                    void *stream);
+
+/* Simulation launches record a failed bounded device-side wait (a TMA tile
+ * that did not arrive within 1 s) in a per-device status word instead of
+ * waiting forever; the drivers check it after every query.  This call
+ * synchronises the device, returns the word in *status (0 or
+ * PBN_ERR_TIMEOUT) and clears it.  (Test hook: with the environment
+ * variable PBN_TEST_STALL_FIRST_TILE=1 at load time, tiled launches never
+ * issue their first tile, so the wait must run out.) */
+int pbn_take_device_status(int *status);
 
 /* ------------------------------------------------------------- statistics */
 

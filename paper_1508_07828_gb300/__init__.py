@@ -66,7 +66,8 @@ class Chains(ctypes.Structure):
 
 class RunCfg(ctypes.Structure):
     _fields_ = [("seed", c_u64), ("perturb_mode", c_i32), ("soi", Soi), ("groups_per_block", c_i32),
-                ("threads_per_block", c_i32), ("threads_per_item", c_i32), ("blocks_per_round", c_i32)]
+                ("threads_per_block", c_i32), ("threads_per_item", c_i32), ("blocks_per_round", c_i32),
+                ("staging", c_i32)]
 
 
 class GrResult(ctypes.Structure):
@@ -167,6 +168,7 @@ def lib():
             L.pbn_engine_submit.argtypes = [c_vp, P(EngineQuery), P(c_i64)]
             L.pbn_engine_step.argtypes = [c_vp, P(EngineStats)]
             L.pbn_engine_poll.argtypes = [c_vp, c_vp, c_i32, P(c_i32)]
+            L.pbn_take_device_status.argtypes = [P(c_i32)]
             L.pbn_last_error.restype = ctypes.c_char_p
             L.pbn_status_string.restype = ctypes.c_char_p
             L.pbn_status_string.argtypes = [ctypes.c_int]
@@ -312,9 +314,20 @@ class ChainSet:
         return b.reshape(self.G * 32, length)[: self.omega]
 
 
-def _cfg(seed, mode, soi_arg, groups_per_block=0, threads_per_block=0, threads_per_item=0, blocks_per_round=0):
+STAGING = {"auto": 0, "smem": 1, "tiles": 2, "global": 3}
+
+
+def _cfg(seed, mode, soi_arg, groups_per_block=0, threads_per_block=0, threads_per_item=0, blocks_per_round=0,
+         staging="auto"):
     return RunCfg(int(seed), int(mode), soi_arg.struct, int(groups_per_block), int(threads_per_block),
-                  int(threads_per_item), int(blocks_per_round))
+                  int(threads_per_item), int(blocks_per_round), STAGING[staging])
+
+
+def pbn_take_device_status() -> int:
+    """Read and clear the device status word (0 or PBN_ERR_TIMEOUT)."""
+    v = c_i32()
+    _check(lib().pbn_take_device_status(ctypes.byref(v)))
+    return v.value
 
 
 def pbn_init_chains(chains: ChainSet, seed: int, mode: int = PER_NODE, stream=None):
@@ -325,9 +338,9 @@ def pbn_init_chains(chains: ChainSet, seed: int, mode: int = PER_NODE, stream=No
 
 def pbn_run_chains(chains: ChainSet, steps: int, seed: int, mode: int = PER_NODE, soi=None,
                    groups_per_block: int = 0, threads_per_block: int = 0, threads_per_item: int = 0,
-                   blocks_per_round: int = 0, stream=None):
+                   blocks_per_round: int = 0, staging: str = "auto", stream=None):
     soi_arg = SoiArg(soi)
-    cfg = _cfg(seed, mode, soi_arg, groups_per_block, threads_per_block, threads_per_item, blocks_per_round)
+    cfg = _cfg(seed, mode, soi_arg, groups_per_block, threads_per_block, threads_per_item, blocks_per_round, staging)
     _check(lib().pbn_run_chains(chains.network.handle, ctypes.byref(cfg), ctypes.byref(chains.c), int(steps),
                                 _stream(stream)))
 

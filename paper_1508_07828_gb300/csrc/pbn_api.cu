@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -95,7 +96,7 @@ int check_soi(const pbn_soi &soi, int n, bool allow_empty) {
 struct LaunchPlan {
   int gpb, threads, T, BPR;
   size_t smem;
-  bool tables_in_smem;
+  int staging;
 };
 
 // Launch shape: chain groups per CTA from the group count and the SM count
@@ -103,16 +104,32 @@ struct LaunchPlan {
 // latency-bound, so 2 threads share an item (each runs 2 Philox blocks, in
 // parallel); otherwise one thread per item, one block per round.
 int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, int threads_req, int T_req,
-                int BPR_req, LaunchPlan *p) {
+                int BPR_req, int staging_req, LaunchPlan *p) {
   const int G = (int)((omega + 31) / 32);
   const int maxs = pbn::sim_max_smem();
   int gpb = gpb_req > 0 ? gpb_req : std::max(1, (G + sm_count() - 1) / sm_count());
   gpb = std::min(gpb, std::max(G, 1));
+  // staging preference: whole tables in shared memory, else TMA tiles, else
+  // global reads (or the requested one)
+  const int prefs[3] = {pbn::STAGE_SMEM, pbn::STAGE_TILES, pbn::STAGE_GLOBAL};
+  // public values: 1 = whole tables in shared memory, 2 = TMA tiles, 3 = global
+  const int wanted = staging_req == 1 ? pbn::STAGE_SMEM
+                     : staging_req == 2 ? pbn::STAGE_TILES
+                     : staging_req == 3 ? pbn::STAGE_GLOBAL
+                                        : -1;
   for (;;) {
-    size_t with = pbn::sim_smem_bytes(net.n, net.F, gpb, mode, true);
-    size_t without = pbn::sim_smem_bytes(net.n, net.F, gpb, mode, false);
-    if ((int64_t)with <= maxs) { p->tables_in_smem = true; p->smem = with; break; }
-    if ((int64_t)without <= maxs) { p->tables_in_smem = false; p->smem = without; break; }
+    bool found = false;
+    for (int st : prefs) {
+      if (wanted >= 0 && st != wanted) continue;
+      const size_t b = pbn::sim_smem_bytes(net.n, net.F, gpb, mode, st, net.tile_bytes);
+      if ((int64_t)b <= maxs) {
+        p->staging = st;
+        p->smem = b;
+        found = true;
+        break;
+      }
+    }
+    if (found) break;
     if (gpb == 1) return fail(PBN_ERR_UNSUPPORTED, "chain state of one group does not fit shared memory");
     gpb = std::max(1, gpb / 2);
   }
@@ -154,7 +171,15 @@ pbn::SimArgs make_args(const pbn::NetDev &net, const pbn_run_cfg &cfg, const pbn
   a.steps = (int)steps;
   a.gpb = plan.gpb;
   a.P32 = net.P32;
-  a.tables_in_smem = plan.tables_in_smem ? 1 : 0;
+  a.staging = plan.staging;
+  a.tiles = net.d_tiles;
+  a.ntiles = net.ntiles;
+  a.tile_bytes = net.tile_bytes;
+  a.status = pbn::device_status();
+  {
+    static const int stall = getenv("PBN_TEST_STALL_FIRST_TILE") ? atoi(getenv("PBN_TEST_STALL_FIRST_TILE")) : 0;
+    a.test_stall = stall;
+  }
   a.soi_size = (ch.bits && ch.bits_cap > 0) ? cfg.soi.size : 0;
   a.soi_val = 0;
   for (int m = 0; m < cfg.soi.size && m < PBN_MAX_SOI; m++) {
@@ -174,8 +199,10 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
                                          (long long)ch.bits_cap, (long long)(ch.length + steps - 1));
   }
   LaunchPlan plan;
+  if (cfg.staging < 0 || cfg.staging > 3) return fail(PBN_ERR_INVALID, "staging %d", cfg.staging);
+  if (!pbn::device_status()) return fail(PBN_ERR_CUDA, "device status word unavailable");
   int rc = plan_launch(net, ch.omega, cfg.perturb_mode, cfg.groups_per_block, cfg.threads_per_block,
-                       cfg.threads_per_item, cfg.blocks_per_round, &plan);
+                       cfg.threads_per_item, cfg.blocks_per_round, cfg.staging, &plan);
   if (rc) return rc;
   // one launch covers at most 2^30 steps; the step counter itself is 64-bit
   const int64_t chunk = 1 << 30;
@@ -193,6 +220,24 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
 }  // namespace
 
 void pbn::set_last_error(const char *msg) { g_err = msg; }
+
+namespace {
+// Reads and clears the device status word (synchronous).
+int take_status(int *out) {
+  int *d = pbn::device_status();
+  if (!d) return fail(PBN_ERR_CUDA, "device status word unavailable");
+  int v = 0;
+  CUDA_TRY(cudaMemcpy(&v, d, sizeof v, cudaMemcpyDeviceToHost), "status read");
+  if (v) CUDA_TRY(cudaMemset(d, 0, sizeof v), "status clear");
+  *out = v;
+  return PBN_OK;
+}
+}  // namespace
+
+extern "C" int pbn_take_device_status(int *status) {
+  if (!status) return fail(PBN_ERR_INVALID, "NULL argument");
+  return take_status(status);
+}
 
 extern "C" {
 
@@ -281,19 +326,47 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
   // update makes the order immaterial to the result.
   std::stable_sort(order.begin(), order.end(),
                    [](const std::pair<uint64_t, int> &a, const std::pair<uint64_t, int> &b) { return a.first < b.first; });
+  // function records in processing order, so that a range of processing
+  // positions is one contiguous range of records (a tile for TMA staging)
   std::vector<uint32_t> node_sorted(n);
-  for (int r = 0; r < n; r++) node_sorted[r] = node[order[r].second];
+  std::vector<uint4> fn_sorted((size_t)F);
+  std::vector<int32_t> tiles(1, 0);
+  int max_tile = 0;
+  {
+    int next = 0, tile_recs = 0;
+    for (int r = 0; r < n; r++) {
+      const int i = order[r].second;
+      const int f0 = d->fn_offset[i], l = d->fn_offset[i + 1] - f0;
+      if (tile_recs + l > pbn::kTileRecords) {
+        tiles.push_back(r);
+        max_tile = std::max(max_tile, tile_recs);
+        tile_recs = 0;
+      }
+      for (int j = 0; j < l; j++) fn_sorted[(size_t)next + j] = fn[(size_t)f0 + j];
+      node_sorted[r] = (uint32_t)i | ((uint32_t)(l - 1) << 12) | ((uint32_t)next << 16);
+      next += l;
+      tile_recs += l;
+    }
+    tiles.push_back(n);
+    max_tile = std::max(max_tile, tile_recs);
+  }
   pbn_net *net = new pbn_net();
   cudaGetDevice(&net->device);
   net->dev.n = n;
   net->dev.F = F;
   net->dev.P32 = P32;
   net->dev.max_l = max_l;
+  net->dev.ntiles = (int)tiles.size() - 1;
+  net->dev.tile_bytes = max_tile * 16;
   cudaError_t e = cudaMalloc(&net->dev.d_fn, sizeof(uint4) * (size_t)F);
   if (e == cudaSuccess) e = cudaMalloc(&net->dev.d_node, sizeof(uint32_t) * (size_t)n);
-  if (e == cudaSuccess) e = cudaMemcpy(net->dev.d_fn, fn.data(), sizeof(uint4) * (size_t)F, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&net->dev.d_tiles, sizeof(int32_t) * tiles.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(net->dev.d_fn, fn_sorted.data(), sizeof(uint4) * (size_t)F, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(net->dev.d_node, node_sorted.data(), sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(net->dev.d_tiles, tiles.data(), sizeof(int32_t) * tiles.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     pbn_free(net);
     return cuda_fail(e, "staging network tables");
@@ -307,6 +380,7 @@ void pbn_free(pbn_net *net) {
   if (!net) return;
   if (net->dev.d_fn) cudaFree(net->dev.d_fn);
   if (net->dev.d_node) cudaFree(net->dev.d_node);
+  if (net->dev.d_tiles) cudaFree(net->dev.d_tiles);
   delete net;
 }
 
@@ -539,12 +613,25 @@ struct Query {
     return PBN_OK;
   }
 
+  // Result of the last statistics launch, read together with the device
+  // status word (one synchronisation): a bounded wait that gave up during
+  // the query fails it here.
   template <typename T>
   int fetch(T *h) {
+    static_assert(sizeof(T) <= 192, "result slot");
+    int *status = pbn::device_status();
+    if (!status) return fail(PBN_ERR_CUDA, "device status word unavailable");
     CUDA_TRY(cudaMemcpyAsync(ws.h_res, d_res, sizeof(T), cudaMemcpyDeviceToHost, s), "result copy");
+    CUDA_TRY(cudaMemcpyAsync((char *)ws.h_res + 192, status, sizeof(int), cudaMemcpyDeviceToHost, s), "status copy");
     CUDA_TRY(cudaStreamSynchronize(s), "stream sync");
     memcpy(h, ws.h_res, sizeof(T));
-    d2h_bytes += sizeof(T);
+    d2h_bytes += sizeof(T) + sizeof(int);
+    int st = 0;
+    memcpy(&st, (char *)ws.h_res + 192, sizeof st);
+    if (st) {
+      CUDA_TRY(cudaMemset(status, 0, sizeof st), "status clear");
+      return fail(st, "a bounded device wait gave up during the query");
+    }
     return PBN_OK;
   }
 
@@ -652,6 +739,11 @@ extern "C" int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_qu
   out->N = r.N;
   out->ones = r.ones;
   out->n4[0] = r.n00; out->n4[1] = r.n01; out->n4[2] = r.n10; out->n4[3] = r.n11;
+  {
+    int st = 0;
+    if ((rc = take_status(&st))) return rc;
+    if (st) return fail(st, "a bounded device wait gave up during the query");
+  }
   out->psi = psi;
   out->length = Q.ch.length;
   out->sample_size = omega * (Q.ch.length - psi);
@@ -738,6 +830,11 @@ extern "C" int pbn_estimate_skart(const pbn_net *net, const pbn_skart_query *q, 
     kappa = k1;
     p = cdiv(p1, omega) * omega;
     eta = kappa * p;
+  }
+  {
+    int st = 0;
+    if ((rc = take_status(&st))) return rc;
+    if (st) return fail(st, "a bounded device wait gave up during the query");
   }
   out->psi = psi;
   out->length = Q.ch.length;

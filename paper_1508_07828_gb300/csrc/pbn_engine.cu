@@ -268,7 +268,7 @@ struct EQuery {
 };
 
 struct Candidate {
-  int S, threads, ipt;
+  int S, threads, ipt, big;
   double ms = 0;
   int64_t updates = 0;
   int trials = 0;
@@ -297,6 +297,8 @@ struct pbn_engine {
   pbn_skart_result *d_sk = nullptr, *h_sk = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int *status = nullptr;                 // device status word of the batched launches
+  std::vector<EQuery *> epoch_queries;   // queries simulated in the current epoch
   size_t graph_smem = 0;
   int graph_threads = 0;
   std::vector<Candidate> cands;
@@ -330,16 +332,18 @@ int smem_limit() {
 // Chain groups per CTA for one query: about threads * ipt items, at most
 // gpb_cap (so that a light epoch still spreads over the SMs), within the
 // shared memory one CTA may use.
-void size_task(const EQuery &q, int threads, int ipt, int gpb_cap, size_t smem_cap, int *gpb_out,
-               bool *tables_out) {
+// Tables that do not fit shared memory are staged as TMA tiles or read from
+// global memory (`big` chooses).
+void size_task(const EQuery &q, int threads, int ipt, int gpb_cap, size_t smem_cap, int big, int *gpb_out,
+               int *staging_out) {
   const NetDev &d = q.dev();
   int gpb = std::max(1, threads * ipt / std::max(1, d.n));
   gpb = std::min(gpb, std::max(1, gpb_cap));
   gpb = std::min(gpb, q.G);
   for (;;) {
-    if (sim_smem_bytes(d.n, d.F, gpb, q.mode, true) <= smem_cap) { *tables_out = true; break; }
-    if (sim_smem_bytes(d.n, d.F, gpb, q.mode, false) <= smem_cap) { *tables_out = false; break; }
-    if (gpb == 1) { *tables_out = false; break; }
+    if (sim_smem_bytes(d.n, d.F, gpb, q.mode, STAGE_SMEM, d.tile_bytes) <= smem_cap) { *staging_out = STAGE_SMEM; break; }
+    if (sim_smem_bytes(d.n, d.F, gpb, q.mode, big, d.tile_bytes) <= smem_cap) { *staging_out = big; break; }
+    if (gpb == 1) { *staging_out = STAGE_GLOBAL; break; }
     gpb = std::max(1, gpb / 2);
   }
   *gpb_out = gpb;
@@ -650,6 +654,8 @@ extern "C" int pbn_engine_create(const pbn_engine_cfg *cfg, void *stream, pbn_en
   ECUDA(cudaMallocHost(&e->h_sk, sizeof(pbn_skart_result)), "engine alloc");
   ECUDA(cudaEventCreate(&e->e0), "event");
   ECUDA(cudaEventCreate(&e->e1), "event");
+  ECUDA(cudaMalloc(&e->status, sizeof(int)), "engine alloc");
+  ECUDA(cudaMemsetAsync(e->status, 0, sizeof(int), e->s), "engine memset");
   memset(e->h_tasks, 0, sizeof(SimArgs) * A);
   memset(e->h_items, 0, sizeof(BatchItem) * e->max_items);
   memset(e->h_reqs, 0, sizeof(StatReq) * A);
@@ -659,18 +665,22 @@ extern "C" int pbn_engine_create(const pbn_engine_cfg *cfg, void *stream, pbn_en
   const int Ss[] = {1024, 4096};
   const int Ts[] = {256, 512};
   const int Is[] = {2, 8};
+  const int Bs[] = {STAGE_TILES, STAGE_GLOBAL};
   for (int S : Ss)
     for (int T : Ts)
-      for (int I : Is) {
-        if (c.steps_per_epoch && S != Ss[0]) continue;
-        if (c.threads_per_block && T != Ts[0]) continue;
-        if (c.items_per_thread && I != Is[0]) continue;
-        Candidate cd;
-        cd.S = c.steps_per_epoch ? c.steps_per_epoch : S;
-        cd.threads = c.threads_per_block ? c.threads_per_block : T;
-        cd.ipt = c.items_per_thread ? c.items_per_thread : I;
-        e->cands.push_back(cd);
-      }
+      for (int I : Is)
+        for (int B : Bs) {
+          if (c.steps_per_epoch && S != Ss[0]) continue;
+          if (c.threads_per_block && T != Ts[0]) continue;
+          if (c.items_per_thread && I != Is[0]) continue;
+          if (B != Bs[0] && (c.steps_per_epoch || c.threads_per_block || c.items_per_thread)) continue;
+          Candidate cd;
+          cd.S = c.steps_per_epoch ? c.steps_per_epoch : S;
+          cd.threads = c.threads_per_block ? c.threads_per_block : T;
+          cd.ipt = c.items_per_thread ? c.items_per_thread : I;
+          cd.big = B;
+          e->cands.push_back(cd);
+        }
   if (e->cands.size() == 1) e->best = 0;
   if (e->best < 0) {
     std::lock_guard<std::mutex> lk(g_tuned_mu);
@@ -700,6 +710,7 @@ extern "C" void pbn_engine_destroy(pbn_engine *e) {
   scratch_free(e->sk);
   cudaFree(e->d_sk); cudaFreeHost(e->h_sk);
   cudaEventDestroy(e->e0); cudaEventDestroy(e->e1);
+  cudaFree(e->status);
   cudaStreamDestroy(e->s);
   delete e;
 }
@@ -757,6 +768,7 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
   if (ci < 0) ci = e->round_robin++ % (int)e->cands.size();
   const Candidate &cand = e->cands[ci];
   size_t smem_cap = (size_t)smem_limit();
+  e->epoch_queries.clear();
   // spread light epochs: at least about two CTAs per SM when the active
   // chain groups allow it
   int64_t total_groups = 0;
@@ -778,9 +790,8 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       if (ntask >= e->cfg.max_active) continue;
       const int64_t D = std::min<int64_t>(cand.S, q.target - q.ch.length);
       if ((rc = reserve_bits(e, q, q.keep_from, q.ch.length + D))) { finish(e, q, rc); continue; }
-      int gpb;
-      bool tables;
-      size_task(q, cand.threads, cand.ipt, gpb_cap, smem_cap, &gpb, &tables);
+      int gpb, staging;
+      size_task(q, cand.threads, cand.ipt, gpb_cap, smem_cap, cand.big, &gpb, &staging);
       const int64_t groups_items = cdiv(q.G, gpb);
       if (nitems + groups_items > e->max_items) continue;   // next epoch
       SimArgs &a = e->h_tasks[ntask];
@@ -801,14 +812,19 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       a.steps = (int)D;
       a.gpb = gpb;
       a.P32 = d.P32;
-      a.tables_in_smem = tables ? 1 : 0;
+      a.staging = staging;
+      a.tiles = d.d_tiles;
+      a.ntiles = d.ntiles;
+      a.tile_bytes = d.tile_bytes;
+      a.status = e->status;
       a.soi_size = (int)q.soi_nodes.size();
       for (size_t m = 0; m < q.soi_nodes.size(); m++) {
         a.soi_node[m] = (uint16_t)q.soi_nodes[m];
         if (q.soi_vals[m]) a.soi_val |= 1u << m;
       }
       a.mode = q.mode;
-      smem = std::max(smem, sim_smem_bytes(d.n, d.F, gpb, q.mode, tables));
+      smem = std::max(smem, sim_smem_bytes(d.n, d.F, gpb, q.mode, staging, d.tile_bytes));
+      e->epoch_queries.push_back(&q);
       order.push_back(std::make_pair(-(int64_t)d.n * gpb * D, ntask));
       task_groups.push_back(std::make_pair(ntask, gpb));
       nitems += (int)groups_items;
@@ -874,6 +890,19 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
   ECUDA(cudaStreamSynchronize(e->s), "epoch sync");
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e->e0, e->e1);
+  {
+    // a bounded device wait that gave up fails every query of this epoch
+    int stv = 0;
+    ECUDA(cudaMemcpy(&stv, e->status, sizeof stv, cudaMemcpyDeviceToHost), "status read");
+    if (stv) {
+      ECUDA(cudaMemset(e->status, 0, sizeof stv), "status clear");
+      for (EQuery *q : e->epoch_queries) {
+        q->sim_D = 0;
+        q->req = -1;
+        finish(e, *q, stv);
+      }
+    }
+  }
   // apply the epoch
   for (auto &qp : e->active) {
     EQuery &q = *qp;

@@ -23,9 +23,18 @@ struct NetDev {
   uint32_t P32 = 0;
   int max_l = 0;
   uint32_t *d_node = nullptr;
-  uint4 *d_fn = nullptr;
+  uint4 *d_fn = nullptr;          // function records in processing order
+  int32_t *d_tiles = nullptr;     // [ntiles+1] first processing position of each tile
+  int ntiles = 0;
+  int tile_bytes = 0;             // largest tile
   int64_t table_bytes = 0;
 };
+
+// Records per TMA tile (24 KB of function records).
+constexpr int kTileRecords = 1536;
+
+// Where a CTA reads the function records from.
+enum Staging { STAGE_GLOBAL = 0, STAGE_SMEM = 1, STAGE_TILES = 2 };
 
 __host__ __device__ __forceinline__ int node_id(uint32_t rec) { return (int)(rec & 0xFFFu); }
 __host__ __device__ __forceinline__ int node_l(uint32_t rec) { return (int)((rec >> 12) & 0xFu) + 1; }
@@ -81,7 +90,12 @@ struct SimArgs {
   int steps;
   int gpb;               // chain groups per block
   uint32_t P32;
-  int tables_in_smem;
+  int staging;           // Staging: global, whole tables in shared memory, or TMA tiles
+  const int32_t *tiles;  // tile starts (processing positions), for STAGE_TILES
+  int ntiles;
+  int tile_bytes;
+  int *status;           // device status word: PBN_ERR_TIMEOUT after a bounded wait gave up
+  int test_stall;        // test hook: never issue tile 0, so its wait must time out
   int soi_size;
   uint16_t soi_node[kMaxSoi];
   uint32_t soi_val;      // bit m = required value of soi_node[m]
@@ -97,7 +111,9 @@ cudaError_t launch_init(const NetDev &net, uint64_t seed, uint32_t *state, int64
 // T = threads per (node, group) item (1, 2 or 4); BPR = Philox blocks per
 // thread per round (T = 1: 1 or 2; T = 2 uses 2; T = 4 uses 1).
 cudaError_t launch_sim(const SimArgs &a, int mode, int T, int BPR, int threads, size_t smem, cudaStream_t s);
-size_t sim_smem_bytes(int n, int F, int gpb, int mode, bool tables_in_smem);
+size_t sim_smem_bytes(int n, int F, int gpb, int mode, int staging, int tile_bytes);
+// Device status word of the simulation kernels on the current device (0 = ok).
+int *device_status();
 int sim_max_smem();
 
 struct StatsScratch {

@@ -27,6 +27,8 @@
 // After each step every group's indicator word of the state of interest
 // (Sec. 3.1) is an AND-reduction across one warp's lanes, stored to the
 // bitstream.
+#include <mutex>
+
 #include "pbn_step.cuh"
 
 namespace pbn {
@@ -49,13 +51,29 @@ __global__ void init_kernel(const __grid_constant__ RoundKeys rk, uint32_t *stat
   }
 }
 
-size_t sim_smem_bytes(int n, int F, int gpb, int mode, bool tables_in_smem) {
+size_t sim_smem_bytes(int n, int F, int gpb, int mode, int staging, int tile_bytes) {
   size_t b = 0;
-  if (tables_in_smem) b += (size_t)F * 16 + (((size_t)n * 4 + 15) & ~(size_t)15);
+  const size_t node_bytes = ((size_t)n * 4 + 15) & ~(size_t)15;
+  if (staging == STAGE_SMEM) b += (size_t)F * 16 + node_bytes;
+  if (staging == STAGE_TILES) b += 2 * (((size_t)tile_bytes + 127) & ~(size_t)127) + node_bytes + 16;
   size_t items = (size_t)n * gpb;
   b += 2 * items * 4;
   if (mode == PBN_PERTURB_GLOBAL) b += items * 4 + 2 * (size_t)gpb * 4;
   return b;
+}
+
+int *device_status() {
+  static std::mutex mu;
+  static int *ptr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptr[dev]) {
+    if (cudaMalloc(&ptr[dev], sizeof(int)) != cudaSuccess) return nullptr;
+    cudaMemset(ptr[dev], 0, sizeof(int));
+  }
+  return ptr[dev];
 }
 
 int sim_max_smem() {

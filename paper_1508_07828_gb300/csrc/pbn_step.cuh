@@ -215,27 +215,89 @@ __device__ __forceinline__ void dispatch_item(int LW, const RoundKeys &rk, uint3
 template <int T>
 constexpr int max_threads() { return T == 1 ? 1024 : 512; }
 
+// ---- TMA tile staging (bulk copies completing on an mbarrier)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// One bulk copy of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) into shared memory, completing the barrier's current phase.
+__device__ __forceinline__ void tile_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for a barrier phase for at most limit_ns nanoseconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_test(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: a 24 KB tile arrives in microseconds
+
 // One CTA's work: advance chain groups g0 .. g0+ngl-1 of task `a` by
 // a.steps transitions.  `rk` are the task's Philox round keys (kernel
 // parameters in the single-task kernel, registers in the batched one).
+// Function records come from shared memory (whole tables), from TMA tiles
+// streamed through two shared buffers (tile u of the launch's sequence
+// s*ntiles + t goes to buffer u & 1), or straight from global memory.
 template <int MODE, int T, int BPR>
 __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &rk, uint32_t g0, int ngl,
                                              unsigned char *smem) {
   const int gpb = a.gpb;
   const int n = a.n;
   const uint32_t P32 = a.P32;
+  const int staging = a.staging;
   const uint4 *fn_s = a.fn;
   const uint32_t *node_s = a.node;
+  uint4 *tilebuf[2] = {nullptr, nullptr};
+  uint64_t *bar = nullptr;
   size_t off = 0;
-  if (a.tables_in_smem) {
+  const size_t node_bytes = ((size_t)n * 4 + 15) & ~(size_t)15;
+  if (staging == STAGE_SMEM) {
     uint4 *f = reinterpret_cast<uint4 *>(smem);
     for (int j = threadIdx.x; j < a.F; j += blockDim.x) f[j] = a.fn[j];
     off = (size_t)a.F * 16;
+    fn_s = f;
+  } else if (staging == STAGE_TILES) {
+    const size_t tb = ((size_t)a.tile_bytes + 127) & ~(size_t)127;
+    tilebuf[0] = reinterpret_cast<uint4 *>(smem);
+    tilebuf[1] = reinterpret_cast<uint4 *>(smem + tb);
+    off = 2 * tb;
+  }
+  if (staging != STAGE_GLOBAL) {
     uint32_t *nd = reinterpret_cast<uint32_t *>(smem + off);
     for (int j = threadIdx.x; j < n; j += blockDim.x) nd[j] = a.node[j];
-    off += ((size_t)n * 4 + 15) & ~(size_t)15;
-    fn_s = f;
+    off += node_bytes;
     node_s = nd;
+  }
+  if (staging == STAGE_TILES) {
+    bar = reinterpret_cast<uint64_t *>(smem + off);
+    off += 16;
   }
   const int items = n * gpb;
   uint32_t *bufA = reinterpret_cast<uint32_t *>(smem + off);
@@ -248,7 +310,27 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
   }
   if (MODE == PBN_PERTURB_GLOBAL)
     for (int j = threadIdx.x; j < 2 * gpb; j += blockDim.x) anyP[j] = 0u;
+  const int ntiles = staging == STAGE_TILES ? a.ntiles : 1;
+  const int64_t total_tiles = (int64_t)a.steps * ntiles;
+  if (staging == STAGE_TILES && threadIdx.x == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
+  // tile u of the sequence into buffer u & 1 (thread 0 only)
+  auto issue = [&](int64_t u) {
+    const int t = (int)(u % ntiles);
+    const int r0 = a.tiles[t], r1 = a.tiles[t + 1];
+    const int rec0 = node_f0(node_s[r0]);
+    const int rec1 = r1 < n ? node_f0(node_s[r1]) : a.F;
+    if (a.test_stall && u == 0) return;  // test hook: this tile never arrives
+    tile_load(tilebuf[u & 1], a.fn + rec0, (uint32_t)(rec1 - rec0) * 16u, &bar[u & 1]);
+  };
+  if (staging == STAGE_TILES && threadIdx.x == 0) {
+    issue(0);
+    if (total_tiles > 1) issue(1);
+  }
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int sub = lane & (T - 1);
@@ -257,7 +339,6 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
   uint32_t *cur = bufA, *nxt = bufB;
   for (int s = 0; s < a.steps; s++) {
     ItemCtx c;
-    c.fn_s = fn_s;
     c.cur = cur;
     c.nxt = nxt;
     c.pbuf = pbuf;
@@ -265,21 +346,45 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
     c.gpb = gpb;
     c.t = a.t0 + (uint64_t)s;
     c.sub = sub;
-    for (int base = 0; base < items; base += nslots) {  // uniform trip count
-      const int q = base + slot;
-      const int r = q / gpb;
-      c.gl = q - r * gpb;
-      c.active = (q < items) && (c.gl < ngl);
-      const uint32_t rec = c.active ? node_s[r] : 0u;
-      c.L = c.active ? node_l(rec) : 0;
-      c.i = node_id(rec);
-      c.f0 = node_f0(rec);
-      c.g = g0 + (uint32_t)c.gl;
-      c.vmask = c.active ? lane_mask(a.omega, c.g) : 0u;
-      const int LW = (int)__reduce_max_sync(kFull, (unsigned)c.L);
-      dispatch_item<MODE, T, BPR>(LW, rk, P32, c);
+    for (int t = 0; t < ntiles; t++) {
+      int p0 = 0, p1 = n;
+      c.fn_s = fn_s;
+      if (staging == STAGE_TILES) {
+        const int64_t u = (int64_t)s * ntiles + t;
+        const bool ok = mbar_wait_bounded(&bar[u & 1], (uint32_t)((u >> 1) & 1), kWaitLimitNs);
+        if (!__syncthreads_and(ok)) {
+          // a tile never arrived: report, let the other buffer's copy land, leave
+          if (threadIdx.x == 0) {
+            atomicExch(a.status, PBN_ERR_TIMEOUT);
+            if (u + 1 < total_tiles) mbar_wait_bounded(&bar[(u + 1) & 1], (uint32_t)(((u + 1) >> 1) & 1), kWaitLimitNs);
+          }
+          __syncthreads();
+          return;
+        }
+        p0 = a.tiles[t];
+        p1 = a.tiles[t + 1];
+        c.fn_s = tilebuf[u & 1] - node_f0(node_s[p0]);
+      }
+      for (int base = p0 * gpb; base < p1 * gpb; base += nslots) {  // uniform trip count
+        const int q = base + slot;
+        const int r = q / gpb;
+        c.gl = q - r * gpb;
+        c.active = (q < p1 * gpb) && (c.gl < ngl);
+        const uint32_t rec = c.active ? node_s[r] : 0u;
+        c.L = c.active ? node_l(rec) : 0;
+        c.i = node_id(rec);
+        c.f0 = node_f0(rec);
+        c.g = g0 + (uint32_t)c.gl;
+        c.vmask = c.active ? lane_mask(a.omega, c.g) : 0u;
+        const int LW = (int)__reduce_max_sync(kFull, (unsigned)c.L);
+        dispatch_item<MODE, T, BPR>(LW, rk, P32, c);
+      }
+      __syncthreads();
+      if (staging == STAGE_TILES && threadIdx.x == 0) {
+        const int64_t u = (int64_t)s * ntiles + t;
+        if (u + 2 < total_tiles) issue(u + 2);
+      }
     }
-    __syncthreads();
     if (MODE == PBN_PERTURB_GLOBAL) {
       for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
         const uint32_t any = c.anyP[idx % gpb];
@@ -310,6 +415,5 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
     if (gl < ngl) a.state[(size_t)(g0 + gl) * n + i] = cur[idx];
   }
 }
-
 
 }  // namespace pbn
