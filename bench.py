@@ -49,12 +49,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sim-only", choices=["mid", "large"], default=None,
+    ap.add_argument("--sim-only", choices=["mid", "large", "wide"], default=None,
                     help="time the simulation kernel alone on a workload (kernel benchmark / profiling case)")
     ap.add_argument("--sim-steps", type=int, default=1024, help="transitions per launch in --sim-only")
     ap.add_argument("--threads-per-item", type=int, default=0)
     ap.add_argument("--blocks-per-round", type=int, default=0)
     ap.add_argument("--groups-per-block", type=int, default=0)
+    ap.add_argument("--staging", choices=["auto", "smem", "tiles", "global"], default="auto",
+                    help="where the function table sits during a --sim-only launch")
+    ap.add_argument("--schedule", choices=["auto", "fused", "select_ahead"], default="auto",
+                    help="step schedule of a --sim-only launch")
     ap.add_argument("--batched", action="store_true",
                     help="64 networks of uneven size: the engine vs the plain one-query-at-a-time loop")
     ap.add_argument("--serve", action="store_true", help="Poisson arrivals over a pool of 200 networks")
@@ -369,7 +373,7 @@ def run_sim_only(args):
         net, soi, cfg = workload()
         omega = cfg["omega"]
     else:
-        net, nodes, cfg = S.large_config()
+        net, nodes, cfg = S.large_config() if args.sim_only == "large" else S.wide_config()
         soi = S.StateOfInterest(nodes, np.ones(len(nodes), dtype=np.uint8))
         omega = cfg["omega"]
     N = P.pbn_load(net)
@@ -377,7 +381,7 @@ def run_sim_only(args):
     cs = P.ChainSet(N, omega, bits_cap=steps)
     P.pbn_init_chains(cs, 5)
     launch = dict(threads_per_item=args.threads_per_item, blocks_per_round=args.blocks_per_round,
-                  groups_per_block=args.groups_per_block)
+                  groups_per_block=args.groups_per_block, staging=args.staging, schedule=args.schedule)
     stream = torch.cuda.current_stream()
 
     def one():
@@ -399,6 +403,7 @@ def run_sim_only(args):
     peak, sms, mhz, src = alu_peak_tops(0)
     achieved = ops / (np.mean(ms) / 1e3) / 1e12
     print(json.dumps({"mode": "sim-only", "workload": args.sim_only, "nodes": int(net.n), "chains": omega,
+                      "functions": int(net.n_functions), "table_bytes": 16 * int(net.n_functions),
                       "steps_per_launch": steps, "launches": args.steps, "ms_per_launch": float(np.mean(ms)),
                       "ms_min": float(np.min(ms)), "updates_per_s": upd / (np.mean(ms) / 1e3),
                       "ns_per_transition": 1e6 * float(np.mean(ms)) / steps,

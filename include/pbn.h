@@ -116,9 +116,22 @@ typedef struct pbn_run_cfg {
     int32_t threads_per_block;  /* 0 = automatic */
     int32_t threads_per_item;   /* threads sharing one (node, chain group) update: 1, 2, 4; 0 = automatic */
     int32_t blocks_per_round;   /* Philox blocks per thread per round when threads_per_item = 1: 1, 2; 0 = auto */
-    int32_t staging;            /* function records: 0 = automatic (shared memory if they fit, else TMA
-                                   tiles), 1 = whole tables in shared memory, 2 = TMA tiles, 3 = global */
+    int32_t staging;            /* function records: 0 = automatic (shared memory if they fit, else read
+                                   from global memory through L1), 1 = whole tables in shared memory,
+                                   2 = TMA tiles streamed through shared memory, 3 = global */
+    int32_t schedule;           /* PBN_SCHEDULE_*: how the steps are laid on the GPU (same chains either way) */
 } pbn_run_cfg;
+
+/* Schedules of pbn_run_chains.  FUSED: one kernel draws each item's category
+ * and updates it, step by step.  SELECT_AHEAD: a first kernel draws the
+ * categories of a chunk of steps for all chains at once (they do not depend
+ * on the state), a second applies them step by step; for few chain groups,
+ * where the fused step waits on its Philox rounds with most SMs idle.
+ * SELECT_AHEAD takes staging 0, 1 or 3 and needs device scratch of up to
+ * 64 MiB per stream (kept by the library, grown on demand).  AUTO: select-ahead
+ * when the chain groups (ceil(omega / 32)) number at most the SMs and its
+ * shared memory fits, else fused. */
+enum { PBN_SCHEDULE_AUTO = 0, PBN_SCHEDULE_FUSED = 1, PBN_SCHEDULE_SELECT_AHEAD = 2 };
 
 /* ---------------------------------------------------------------- network */
 
@@ -143,7 +156,9 @@ int pbn_init_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *chai
  * Alg. GR / Alg. 3 / Alg. 4).  Writes the indicator bits of positions
  * length .. length+steps-1 that fall at or after bits_base; the caller must
  * have made bits_cap cover them.  chains->length += steps.
- * Errors: PBN_ERR_INVALID (SOI, capacity), PBN_ERR_CUDA. */
+ * Errors: PBN_ERR_INVALID (SOI, capacity, launch shape), PBN_ERR_UNSUPPORTED
+ * (a requested schedule or staging that does not fit shared memory),
+ * PBN_ERR_OOM (select-ahead scratch), PBN_ERR_CUDA. */
 int pbn_run_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *chains, int64_t steps,
                    void *stream);
 

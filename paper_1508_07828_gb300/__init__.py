@@ -67,7 +67,7 @@ class Chains(ctypes.Structure):
 class RunCfg(ctypes.Structure):
     _fields_ = [("seed", c_u64), ("perturb_mode", c_i32), ("soi", Soi), ("groups_per_block", c_i32),
                 ("threads_per_block", c_i32), ("threads_per_item", c_i32), ("blocks_per_round", c_i32),
-                ("staging", c_i32)]
+                ("staging", c_i32), ("schedule", c_i32)]
 
 
 class GrResult(ctypes.Structure):
@@ -315,12 +315,13 @@ class ChainSet:
 
 
 STAGING = {"auto": 0, "smem": 1, "tiles": 2, "global": 3}
+SCHEDULE = {"auto": 0, "fused": 1, "select_ahead": 2}
 
 
 def _cfg(seed, mode, soi_arg, groups_per_block=0, threads_per_block=0, threads_per_item=0, blocks_per_round=0,
-         staging="auto"):
+         staging="auto", schedule="auto"):
     return RunCfg(int(seed), int(mode), soi_arg.struct, int(groups_per_block), int(threads_per_block),
-                  int(threads_per_item), int(blocks_per_round), STAGING[staging])
+                  int(threads_per_item), int(blocks_per_round), STAGING[staging], SCHEDULE[schedule])
 
 
 def pbn_take_device_status() -> int:
@@ -338,9 +339,10 @@ def pbn_init_chains(chains: ChainSet, seed: int, mode: int = PER_NODE, stream=No
 
 def pbn_run_chains(chains: ChainSet, steps: int, seed: int, mode: int = PER_NODE, soi=None,
                    groups_per_block: int = 0, threads_per_block: int = 0, threads_per_item: int = 0,
-                   blocks_per_round: int = 0, staging: str = "auto", stream=None):
+                   blocks_per_round: int = 0, staging: str = "auto", schedule: str = "auto", stream=None):
     soi_arg = SoiArg(soi)
-    cfg = _cfg(seed, mode, soi_arg, groups_per_block, threads_per_block, threads_per_item, blocks_per_round, staging)
+    cfg = _cfg(seed, mode, soi_arg, groups_per_block, threads_per_block, threads_per_item, blocks_per_round, staging,
+               schedule)
     _check(lib().pbn_run_chains(chains.network.handle, ctypes.byref(cfg), ctypes.byref(chains.c), int(steps),
                                 _stream(stream)))
 

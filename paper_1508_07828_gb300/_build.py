@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpbn_gb300.so")
 
-SOURCES = ["pbn_sim.cu", "pbn_stats.cu", "pbn_api.cu", "pbn_noalloc.cu", "pbn_engine.cu"]
+SOURCES = ["pbn_sim.cu", "pbn_split.cu", "pbn_stats.cu", "pbn_api.cu", "pbn_noalloc.cu", "pbn_engine.cu"]
 HEADERS = [os.path.join(CSRC, "pbn_internal.cuh"), os.path.join(CSRC, "pbn_step.cuh"),
            os.path.join(CSRC, "pbn_stats.cuh"),
            os.path.join(INCLUDE, "pbn.h")]

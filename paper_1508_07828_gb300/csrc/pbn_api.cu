@@ -109,9 +109,11 @@ int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, in
   const int maxs = pbn::sim_max_smem();
   int gpb = gpb_req > 0 ? gpb_req : std::max(1, (G + sm_count() - 1) / sm_count());
   gpb = std::min(gpb, std::max(G, 1));
-  // staging preference: whole tables in shared memory, else TMA tiles, else
-  // global reads (or the requested one)
-  const int prefs[3] = {pbn::STAGE_SMEM, pbn::STAGE_TILES, pbn::STAGE_GLOBAL};
+  // staging preference: whole tables in shared memory, else global reads
+  // (the records a warp touches stay in L1; measured faster than TMA tiles,
+  // whose buffers cost chain groups per CTA and whose per-tile barriers cost
+  // time); TMA tiles only when requested
+  const int prefs[3] = {pbn::STAGE_SMEM, pbn::STAGE_GLOBAL, pbn::STAGE_TILES};
   // public values: 1 = whole tables in shared memory, 2 = TMA tiles, 3 = global
   const int wanted = staging_req == 1 ? pbn::STAGE_SMEM
                      : staging_req == 2 ? pbn::STAGE_TILES
@@ -189,7 +191,137 @@ pbn::SimArgs make_args(const pbn::NetDev &net, const pbn_run_cfg &cfg, const pbn
   return a;
 }
 
-int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, cudaStream_t s) {
+// Select-ahead scratch per (device, stream): the category words of one chunk
+// and, for global perturbation, their per-group OR.  Grown on the stream, so
+// launches already queued keep the old buffer until they finish.
+struct SelectScratch {
+  uint32_t *planes = nullptr;
+  size_t planes_words = 0;
+  uint32_t *anyw = nullptr;
+  size_t any_words = 0;
+};
+std::mutex g_sel_mu;
+std::map<std::pair<int, cudaStream_t>, SelectScratch> g_sel;
+
+int grow(uint32_t *&buf, size_t &have, size_t words, cudaStream_t s) {
+  if (words <= have) return PBN_OK;
+  if (buf) cudaFreeAsync(buf, s);
+  buf = nullptr;
+  have = 0;
+  cudaError_t e = cudaMallocAsync(&buf, words * 4, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? PBN_ERR_OOM : PBN_ERR_CUDA, "select-ahead scratch: %s",
+                cudaGetErrorString(e));
+  }
+  have = words;
+  return PBN_OK;
+}
+
+// Largest chunk of the select-ahead schedule: 1024 steps, or fewer when the
+// category words of all groups would exceed 64 MiB (they stay in L2 between
+// the two kernels at the chain counts this schedule is for).
+constexpr int64_t kSelectMaxSteps = 1024;
+constexpr int64_t kSelectBudgetBytes = 64ll << 20;
+
+struct SelectPlan {
+  int gpb, threads, staging, W, ring, T;
+  size_t smem;
+};
+
+// Launch shape of the select-ahead schedule, or PBN_ERR_UNSUPPORTED when its
+// shared memory does not fit (staging_req: public values 0, 1, 3; 2 = tiles
+// is not supported).
+int plan_select(const pbn::NetDev &net, int64_t omega, int gpb_req, int threads_req, int T_req, int staging_req,
+                SelectPlan *p) {
+  const int G = (int)((omega + 31) / 32);
+  const int maxs = pbn::sim_max_smem();
+  if (staging_req == 2) return fail(PBN_ERR_UNSUPPORTED, "select-ahead schedule with TMA tiles");
+  int gpb = gpb_req > 0 ? gpb_req : std::max(1, (G + sm_count() - 1) / sm_count());
+  gpb = std::min(gpb, std::max(G, 1));
+  const int W = (net.F + 3) & ~3;
+  // a deep ring (latency of the category words hidden 7 steps ahead) before
+  // tables in shared memory; the records a warp reads stay in L1 otherwise
+  const int opts[4][2] = {{8, pbn::STAGE_SMEM}, {8, pbn::STAGE_GLOBAL}, {3, pbn::STAGE_SMEM}, {3, pbn::STAGE_GLOBAL}};
+  for (;;) {
+    bool found = false;
+    for (const auto &o : opts) {
+      const int st = o[1];
+      if (staging_req == 1 && st != pbn::STAGE_SMEM) continue;
+      if (staging_req == 3 && st != pbn::STAGE_GLOBAL) continue;
+      const size_t b = pbn::apply_smem_bytes(net.n, net.F, gpb, W, st, o[0]);
+      if ((int64_t)b <= maxs) {
+        p->staging = st;
+        p->ring = o[0];
+        p->smem = b;
+        found = true;
+        break;
+      }
+    }
+    if (found) break;
+    if (gpb == 1 || gpb_req > 0)
+      return fail(PBN_ERR_UNSUPPORTED, "select-ahead shared memory does not fit (n %d, F %d)", net.n, net.F);
+    gpb = std::max(1, gpb / 2);
+  }
+  // 4 threads share an item's truth tables unless asked otherwise: the step is
+  // a chain of dependent operations, so spreading it over more warps pays
+  const int T = T_req > 0 ? T_req : 4;
+  if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
+  const int items = net.n * gpb;
+  const int tmax = pbn::apply_threads_limit(T);
+  int threads = threads_req > 0 ? threads_req : std::min(tmax, std::max(32, (items * T + 31) / 32 * 32));
+  if (threads % 32 || threads > tmax || threads < 32)
+    return fail(PBN_ERR_INVALID, "threads_per_block %d (a multiple of 32, at most %d here)", threads, tmax);
+  p->T = T;
+  p->gpb = gpb;
+  p->threads = threads;
+  p->W = W;
+  return PBN_OK;
+}
+
+int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, bool record,
+                     const SelectPlan &sp, cudaStream_t s, int64_t *launches) {
+  const int G = (int)((ch.omega + 31) / 32);
+  const int64_t per_step = (int64_t)G * sp.W * 4;
+  const int64_t C = std::max<int64_t>(1, std::min(kSelectMaxSteps, kSelectBudgetBytes / per_step));
+  const int64_t first = std::min(C, steps);
+  SelectScratch *sc;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_sel_mu);
+    sc = &g_sel[std::make_pair(dev, s)];
+  }
+  int rc = grow(sc->planes, sc->planes_words, (size_t)first * G * sp.W, s);
+  if (rc) return rc;
+  if (cfg.perturb_mode == PBN_PERTURB_GLOBAL && (rc = grow(sc->anyw, sc->any_words, (size_t)first * G, s)))
+    return rc;
+  LaunchPlan lp;
+  lp.gpb = sp.gpb;
+  lp.threads = sp.threads;
+  lp.T = 1;
+  lp.BPR = 1;
+  lp.smem = sp.smem;
+  lp.staging = sp.staging;
+  for (int64_t done = 0; done < steps; done += C) {
+    const int64_t k = std::min(C, steps - done);
+    pbn::SimArgs a = make_args(net, cfg, ch, k, lp);
+    if (!record) a.soi_size = 0;
+    a.W = sp.W;
+    a.planes = sc->planes;
+    a.anyw = sc->anyw;
+    if (cfg.perturb_mode == PBN_PERTURB_GLOBAL)
+      CUDA_TRY(cudaMemsetAsync(sc->anyw, 0, (size_t)k * G * 4, s), "select-ahead clear");
+    CUDA_TRY(pbn::launch_select(a, cfg.perturb_mode, 1, s), "select launch");
+    CUDA_TRY(pbn::launch_apply(a, cfg.perturb_mode, sp.ring, sp.T, sp.threads, sp.smem, s), "apply launch");
+    ch.length += k;
+    if (launches) *launches += 2;
+  }
+  return PBN_OK;
+}
+
+int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, cudaStream_t s,
+              int64_t *launches = nullptr) {
   if (steps < 0) return fail(PBN_ERR_INVALID, "negative step count");
   if (steps == 0) return PBN_OK;
   const bool record = ch.bits && ch.bits_cap > 0 && cfg.soi.size > 0;
@@ -200,7 +332,22 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
   }
   LaunchPlan plan;
   if (cfg.staging < 0 || cfg.staging > 3) return fail(PBN_ERR_INVALID, "staging %d", cfg.staging);
+  if (cfg.schedule < PBN_SCHEDULE_AUTO || cfg.schedule > PBN_SCHEDULE_SELECT_AHEAD)
+    return fail(PBN_ERR_INVALID, "schedule %d", cfg.schedule);
   if (!pbn::device_status()) return fail(PBN_ERR_CUDA, "device status word unavailable");
+  const int G = (int)((ch.omega + 31) / 32);
+  const bool want_select = cfg.schedule == PBN_SCHEDULE_SELECT_AHEAD ||
+                           (cfg.schedule == PBN_SCHEDULE_AUTO && G <= sm_count() && cfg.staging != 2 &&
+                            cfg.threads_per_item == 0 && cfg.blocks_per_round == 0);
+  if (want_select) {
+    SelectPlan sp;
+    const std::string saved = g_err;
+    int rc = plan_select(net, ch.omega, cfg.groups_per_block, cfg.threads_per_block, cfg.threads_per_item,
+                         cfg.staging, &sp);
+    if (rc == PBN_OK) return run_select_ahead(net, cfg, ch, steps, record, sp, s, launches);
+    if (cfg.schedule == PBN_SCHEDULE_SELECT_AHEAD) return rc;
+    g_err = saved;  // automatic choice: fall back to the fused schedule
+  }
   int rc = plan_launch(net, ch.omega, cfg.perturb_mode, cfg.groups_per_block, cfg.threads_per_block,
                        cfg.threads_per_item, cfg.blocks_per_round, cfg.staging, &plan);
   if (rc) return rc;
@@ -213,6 +360,7 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
     CUDA_TRY(pbn::launch_sim(a, cfg.perturb_mode, plan.T, plan.BPR, plan.threads, plan.smem, s),
              "simulation launch");
     ch.length += k;
+    if (launches) *launches += 1;
   }
   return PBN_OK;
 }
@@ -598,10 +746,10 @@ struct Query {
     if (!a || !b) return fail(PBN_ERR_CUDA, "event creation failed");
     n_events += 2;
     CUDA_TRY(cudaEventRecord(a, s), "event");
-    rc = run_steps(net, cfg, ch, steps, s);
+    int64_t launches = 0;
+    rc = run_steps(net, cfg, ch, steps, s, &launches);
     if (rc) return rc;
     CUDA_TRY(cudaEventRecord(b, s), "event");
-    const int64_t launches = (steps + (1ll << 30) - 1) >> 30;
     sim_launches += launches;
     kernel_launches += launches;
     sim_items += steps * (int64_t)net.n * ((ch.omega + 31) / 32);

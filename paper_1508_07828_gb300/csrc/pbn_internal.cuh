@@ -100,6 +100,9 @@ struct SimArgs {
   uint16_t soi_node[kMaxSoi];
   uint32_t soi_val;      // bit m = required value of soi_node[m]
   int mode;              // perturbation reading (batched kernel only)
+  int W;                 // select-ahead: category words per (step, group), F rounded up to 4
+  uint32_t *planes;      // select-ahead: category words [steps][G][W] of the chunk
+  uint32_t *anyw;        // select-ahead, global perturbation: [steps][G] OR of the perturbed lanes
 };
 static_assert(sizeof(SimArgs) % 4 == 0, "SimArgs is copied word by word");
 
@@ -112,6 +115,13 @@ cudaError_t launch_init(const NetDev &net, uint64_t seed, uint32_t *state, int64
 // thread per round (T = 1: 1 or 2; T = 2 uses 2; T = 4 uses 1).
 cudaError_t launch_sim(const SimArgs &a, int mode, int T, int BPR, int threads, size_t smem, cudaStream_t s);
 size_t sim_smem_bytes(int n, int F, int gpb, int mode, int staging, int tile_bytes);
+// Select-ahead schedule (pbn_split.cu): the category words of a.steps steps
+// of all groups, then their application (a.staging: STAGE_SMEM or STAGE_GLOBAL).
+cudaError_t launch_select(const SimArgs &a, int mode, int BPR, cudaStream_t s);
+// T = threads per (node, group) item: 1, 2 or 4 (each a share of the depth-5 tree).
+cudaError_t launch_apply(const SimArgs &a, int mode, int ring, int T, int threads, size_t smem, cudaStream_t s);
+size_t apply_smem_bytes(int n, int F, int gpb, int W, int staging, int ring);
+int apply_threads_limit(int T);  // largest CTA of the apply variant for T
 // Device status word of the simulation kernels on the current device (0 = ok).
 int *device_status();
 int sim_max_smem();

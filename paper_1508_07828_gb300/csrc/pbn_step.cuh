@@ -83,11 +83,13 @@ struct ItemCtx {
   int sub;
 };
 
-// One item of one transition with LW (warp-uniform) category bounds; bound 0
-// is P32, bound m is T_{m-1}; bounds m >= L are unreachable (all lanes below).
-template <int LW, int MODE, int T, int BPR>
-__device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
-  uint32_t ts[LW], und[LW], lt[LW];
+// Category draw of one item of one transition with LW (warp-uniform)
+// category bounds; bound 0 is P32, bound m is T_{m-1}; bounds m >= L are
+// unreachable (all lanes below).  On return lt[m] holds the lanes whose
+// uniform lies below bound m (complete in every one of the T threads).
+template <int LW, int T, int BPR>
+__device__ __forceinline__ void draw_below(const RoundKeys &rk, uint32_t P32, const ItemCtx &c, uint32_t (&lt)[LW]) {
+  uint32_t ts[LW], und[LW];
 #pragma unroll
   for (int m = 0; m < LW; m++) {
     const bool real = m < c.L;
@@ -147,17 +149,27 @@ __device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, con
       und[m] &= u[m];
     }
   }
-  // lanes of function j: below bound j+1 and not below bound j
-  uint32_t sel[LW];
-  {
-    uint32_t prev = lt[0];
+}
+
+// Lanes of function j: below bound j+1 and not below bound j.
+template <int LW>
+__device__ __forceinline__ void select_masks(const uint32_t (&lt)[LW], uint32_t vmask, uint32_t (&sel)[LW]) {
+  uint32_t prev = lt[0];
 #pragma unroll
-    for (int j = 0; j < LW; j++) {
-      const uint32_t upto = (j + 1 < LW) ? lt[j + 1] : kFull;
-      sel[j] = upto & ~prev & c.vmask;
-      prev = upto;
-    }
+  for (int j = 0; j < LW; j++) {
+    const uint32_t upto = (j + 1 < LW) ? lt[j + 1] : kFull;
+    sel[j] = upto & ~prev & vmask;
+    prev = upto;
   }
+}
+
+// One item of one transition: category draw, then the selected functions.
+template <int LW, int MODE, int T, int BPR>
+__device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
+  uint32_t lt[LW];
+  draw_below<LW, T, BPR>(rk, P32, c, lt);
+  uint32_t sel[LW];
+  select_masks<LW>(lt, c.vmask, sel);
   uint32_t fword = 0u;
 #pragma unroll
   for (int p0 = 0; p0 < LW; p0 += T) {
@@ -333,6 +345,10 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
   }
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // lane m's state-of-interest node, read once (a per-lane index into the
+  // parameter bank would serialise every step)
+  const int my_soi = lane < a.soi_size ? (int)a.soi_node[lane] : 0;
+  const bool my_val = (a.soi_val >> lane) & 1u;
   const int sub = lane & (T - 1);
   const int slot = threadIdx.x / T;
   const int nslots = blockDim.x / T;
@@ -399,8 +415,8 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
       for (int gl = warp; gl < ngl; gl += nwarps) {
         uint32_t v = kFull;
         if (lane < a.soi_size) {
-          const uint32_t w = nxt[a.soi_node[lane] * gpb + gl];
-          v = ((a.soi_val >> lane) & 1u) ? w : ~w;
+          const uint32_t w = nxt[my_soi * gpb + gl];
+          v = my_val ? w : ~w;
         }
         v = __reduce_and_sync(kFull, v);
         if (lane == 0 && col >= 0) a.bits[(size_t)(g0 + gl) * a.bits_cap + col] = v & lane_mask(a.omega, g0 + gl);

@@ -163,6 +163,15 @@ def large_config(seed: int = BASE_SEED + 2, n: int = 2000) -> tuple:
     return net, np.arange(10, dtype=np.int32), dict(omega=16384, rhat=1.05, rel=0.01, alpha=0.05)
 
 
+def wide_config(seed: int = BASE_SEED + 5, n: int = 4096) -> tuple:
+    """n=4096; 4-8 functions per node; 2-5 parents with scale-free weights;
+    biased truth tables; p=0.001; 16384 chains; state of interest nodes 0..9.
+    About 25,000 functions (roughly 400 KB of function records): a network
+    whose table does not fit one block's shared memory."""
+    net = random_pbn(seed, n, (4, 8), (2, 5), "biased", "powerlaw", 0.001, f"wide-n{n}")
+    return net, np.arange(10, dtype=np.int32), dict(omega=16384, rhat=1.05, rel=0.01, alpha=0.05)
+
+
 def _log_uniform_int(rng, lo, hi):
     return int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
 

@@ -51,7 +51,7 @@ STRUCTS = {
     "Soi": ("pbn_soi", ["size", "nodes", "values"]),
     "Chains": ("pbn_chains", ["omega", "state", "bits", "bits_cap", "bits_base", "length"]),
     "RunCfg": ("pbn_run_cfg", ["seed", "perturb_mode", "soi", "groups_per_block", "threads_per_block",
-                               "threads_per_item", "blocks_per_round", "staging"]),
+                               "threads_per_item", "blocks_per_round", "staging", "schedule"]),
     "GrResult": ("pbn_gr_result", ["rhat", "W", "B", "sigma2", "S1", "S2_lo", "S2_hi"]),
     "TwoStateResult": ("pbn_two_state_result", ["n00", "n01", "n10", "n11", "ones", "alpha", "beta", "prob", "M",
                                                 "N", "status"]),

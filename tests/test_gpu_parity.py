@@ -65,12 +65,13 @@ def _gpu_run(P, net, soi, omega, seed, mode, chunks, **launch):
     return cs, init, states
 
 
+@pytest.mark.parametrize("schedule", ["fused", "select_ahead"])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("name,net,soi,omega", NETS, ids=[x[0] for x in NETS])
-def test_trajectories_bit_exact(P, name, net, soi, omega, mode):
+def test_trajectories_bit_exact(P, name, net, soi, omega, mode, schedule):
     seed = 0xC0FFEE + omega
     chunks = [50, 27]
-    cs, init, states = _gpu_run(P, net, soi, omega, seed, mode, chunks)
+    cs, init, states = _gpu_run(P, net, soi, omega, seed, mode, chunks, schedule=schedule)
     ref = oracle.init_states(net, seed, omega)
     assert np.array_equal(init, ref)
     t0 = 0
@@ -111,14 +112,57 @@ def test_item_thread_variants_bit_exact(P, name, launch):
         assert np.array_equal(cs.indicator_numpy(0, 33), ind)
 
 
-def test_max_nodes_and_max_soi(P):
+@pytest.mark.parametrize("schedule", ["fused", "select_ahead"])
+def test_max_nodes_and_max_soi(P, schedule):
     net = S.random_pbn(31, 4096, (1, 2), (0, 5), "biased", "uniform", 0.002)
     soi = S.StateOfInterest(np.arange(0, 4096, 128), np.arange(32) % 2)
-    cs, init, states = _gpu_run(P, net, soi, 33, 17, 0, [6])
+    cs, init, states = _gpu_run(P, net, soi, 33, 17, 0, [6], schedule=schedule)
     ref0 = oracle.init_states(net, 17, 33)
     ref, ind = oracle.simulate(net, 0, 17, ref0, 0, 6, soi)
     assert np.array_equal(states[-1], ref)
     assert np.array_equal(cs.indicator_numpy(0, 6), ind)
+
+
+SA_LAUNCHES = [dict(groups_per_block=2), dict(groups_per_block=3, threads_per_block=64), dict(threads_per_block=32),
+               dict(staging="smem"), dict(staging="global"), dict(groups_per_block=7, threads_per_block=1024),
+               dict(threads_per_item=1), dict(threads_per_item=2), dict(threads_per_item=2, staging="global"),
+               dict(threads_per_item=4, groups_per_block=3, threads_per_block=64)]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("launch", SA_LAUNCHES, ids=[str(x) for x in SA_LAUNCHES])
+def test_select_ahead_launch_shapes(P, launch, mode):
+    """The select-ahead schedule with several groups per CTA, fewer threads
+    than items, and either staging: the fused schedule's chains."""
+    net, soi = S.mid_config()[:2]
+    a, _, sa = _gpu_run(P, net, soi, 200, 3, mode, [40], schedule="fused")
+    b, _, sb = _gpu_run(P, net, soi, 200, 3, mode, [40], schedule="select_ahead", **launch)
+    assert np.array_equal(sa[-1], sb[-1])
+    assert np.array_equal(a.indicator_numpy(0, 40), b.indicator_numpy(0, 40))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_select_ahead_chunks_and_calls(P, mode):
+    """Select-ahead chunks of 1024 steps: calls of 1, 1023, 1025 and 2100
+    steps (chunk edges inside and at the ends of calls) against the oracle."""
+    net, soi = next((x[1], x[2]) for x in NETS if x[0] == "k0-mix")
+    chunks = [1, 1023, 1025, 2100]
+    cs, init, states = _gpu_run(P, net, soi, 45, 99, mode, chunks, schedule="select_ahead")
+    ref = oracle.init_states(net, 99, 45)
+    t0, inds = 0, []
+    for k, got in zip(chunks, states):
+        ref, ind = oracle.simulate(net, mode, 99, ref, t0, k, soi)
+        inds.append(ind)
+        assert np.array_equal(got, ref), t0
+        t0 += k
+    assert np.array_equal(cs.indicator_numpy(0, t0), np.concatenate(inds, axis=1))
+
+
+def test_select_ahead_refuses_tiles(P):
+    net, soi = S.mid_config()[:2]
+    with pytest.raises(P.PbnError) as e:
+        _gpu_run(P, net, soi, 64, 3, 0, [4], schedule="select_ahead", staging="tiles")
+    assert e.value.status == P.PBN_ERR_UNSUPPORTED
 
 
 def test_gelman_rubin_parity(P):

@@ -1,8 +1,9 @@
 """A bounded device-side wait that runs out: a TMA tile that is never issued
 (test hook PBN_TEST_STALL_FIRST_TILE=1, read when the library loads) makes
-the simulation kernel give up after its 1 s limit, record PBN_ERR_TIMEOUT in
-the device status word and return; the host reads the status, the driver
-fails the query with PBN_ERR_TIMEOUT, and the CUDA context stays usable."""
+the fused simulation kernel give up after its 1 s limit, record
+PBN_ERR_TIMEOUT in the device status word and return; the host reads the
+status, a driver query reading results after such a launch fails with
+PBN_ERR_TIMEOUT, and the CUDA context stays usable."""
 import os
 import subprocess
 import sys
@@ -21,22 +22,26 @@ CHILD = textwrap.dedent("""
     import torch
     import pbn_synth as S
     import paper_1508_07828_gb300 as P
-    # tables of about 380 KB: shared memory cannot hold them, so launches stage TMA tiles
+    # tables of about 380 KB, streamed through shared memory as TMA tiles
     net = S.random_pbn(3, 4096, (4, 8), (2, 4), "biased", "uniform", 0.01)
     soi = S.StateOfInterest([0], [1])
     N = P.pbn_load(net)
     cs = P.ChainSet(N, 64, bits_cap=16)
     P.pbn_init_chains(cs, 1)
-    P.pbn_run_chains(cs, 4, 1, P.PER_NODE, soi, staging="tiles")
+    P.pbn_run_chains(cs, 4, 1, P.PER_NODE, soi, staging="tiles", schedule="fused")
     torch.cuda.synchronize()
     st = P.pbn_take_device_status()
     assert st == P.PBN_ERR_TIMEOUT, st
     assert P.pbn_take_device_status() == 0          # cleared
+    # a stalled launch queued ahead of a query on the same stream: the query's
+    # first result read also reads the status word and fails the query
+    P.pbn_run_chains(cs, 4, 1, P.PER_NODE, soi, staging="tiles", schedule="fused")
     try:
         P.pbn_estimate_two_state(N, soi, omega=64, seed=2, psi0=64, r=0.05, max_length=256)
         raise SystemExit("expected a timeout")
     except P.PbnError as e:
         assert e.status == P.PBN_ERR_TIMEOUT, e
+    assert P.pbn_take_device_status() == 0          # the failed query cleared it
     # the context is still usable: untiled launches and plain torch work
     P.pbn_run_chains(cs, 4, 1, P.PER_NODE, soi, staging="global")
     torch.cuda.synchronize()
