@@ -269,7 +269,11 @@ int plan_select(const pbn::NetDev &net, int64_t omega, int gpb_req, int threads_
   if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
   const int items = net.n * gpb;
   const int tmax = pbn::apply_threads_limit(T);
-  int threads = threads_req > 0 ? threads_req : std::min(tmax, std::max(32, (items * T + 31) / 32 * 32));
+  // with T > 1 and one item per T threads, one more warp feeds the others
+  const int item_threads = (items * T + 31) / 32 * 32;
+  int threads = threads_req > 0                                  ? threads_req
+                : (T > 1 && item_threads + 32 <= tmax)           ? item_threads + 32
+                                                                 : std::min(tmax, std::max(32, item_threads));
   if (threads % 32 || threads > tmax || threads < 32)
     return fail(PBN_ERR_INVALID, "threads_per_block %d (a multiple of 32, at most %d here)", threads, tmax);
   p->T = T;

@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
     const int i = idx / gpb, gl = idx - i * gpb;
     cur[idx] = gl < ngl ? a.state[(size_t)(g0 + gl) * n + i] : 0u;
   }
+  __syncthreads();  // tables and state staged before any thread reads another's records
   // step s's words of this CTA's groups: one contiguous run of ngl * W words
   const int chunks16 = ngl * W / 4;
   auto issue = [&](int s) {
@@ -263,7 +264,6 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
     }
     async_commit();  // one group per step, empty past the end, so the wait count stays uniform
   };
-  for (int s = 0; s < kRing - 1; s++) issue(s);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   // lane m's state-of-interest node, read once (a per-lane index into the
   // parameter bank would serialise every step)
@@ -322,46 +322,87 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
       nxt[idx] = (any & (cur[idx] ^ P)) | (~any & fword);
     }
   };
-  if (T > 1 && items * T <= (int)blockDim.x) {
-    // one item per T threads for the whole launch: everything that does not
-    // change from step to step stays in registers
+  if (T > 1 && items * T <= (int)blockDim.x - 32) {
+    // One item per T threads for the whole launch, everything that does not
+    // change from step to step in registers; the last warp is the producer:
+    // it waits for the category words, writes the indicator and requests the
+    // words of later steps, so the item warps only compute between barriers.
+    const bool producer = warp == nwarps - 1;
     const int it = threadIdx.x / T, sub = threadIdx.x & (T - 1);
     const int r = it / gpb, gl = it - r * gpb;
-    const bool active = it < items && gl < ngl;
+    const bool active = !producer && it < items && gl < ngl;
     const uint32_t rec = active ? node_s[r] : 0u;
     const int L = active ? node_l(rec) : 0;
     const int f0 = node_f0(rec);
     const int idx = node_id(rec) * gpb + gl;
     const uint32_t vmask = active ? lane_mask(a.omega, g0 + gl) : 0u;
     const int LW = (int)__reduce_max_sync(kFull, (unsigned)L);
-    const int woff = gl * W + f0;
+    const int woff = active ? gl * W + f0 : 0;
+    const int slot_words = gpb * W;
     ResidentItem<T> R;
 #pragma unroll
     for (int c = 0; c < kResident; c++) {
       if (c < L) R.load(c, fn_s[f0 + c], tt_replicated, gpb, gl, sub);
       else R.clear(c);
     }
-    for (int s = 0; s < a.steps; s++) {
-      step_top(s);
-      const uint32_t *slot = ring + (size_t)(s % kRing) * gpb * W;
-      const uint32_t *w = slot + woff;
-      const uint32_t P = active ? w[0] : 0u;
-      uint32_t rest = vmask & ~P;
-      uint32_t sel = L > 1 ? w[1] : (L == 1 ? rest : 0u);
-      rest &= ~sel;
-      uint32_t fword = sel & R.eval(0, cur, sub);
-      if (LW > 1) {
-        sel = L > 2 ? w[2] : (L == 2 ? rest : 0u);
-        rest &= ~sel;
-        fword |= sel & R.eval(1, cur, sub);
-        if (LW > kResident) eval_rest(kResident, LW, L, f0, gl, sub, w, rest, fword);
+    auto issue_warp = [&](int s) {
+      if (s < a.steps) {
+        const uint32_t *src = a.planes + ((size_t)s * a.G + g0) * W;
+        uint32_t *dst = ring + (size_t)(s % kRing) * slot_words;
+        for (int j = lane; j < chunks16; j += 32) copy16_async(dst + 4 * j, src + 4 * j);
+        if (MODE == PBN_PERTURB_GLOBAL)
+          for (int g = lane; g < ngl; g += 32)
+            copy4_async(ring_any + (s % kRing) * gpbA + g, a.anyw + (size_t)s * a.G + g0 + g);
       }
-      if (active && sub == 0) finish(idx, gl, P, fword, ring_any + (s % kRing) * gpbA);
+      async_commit();
+    };
+    auto indicator_warp = [&](const uint32_t *st, int s) {
+      if (a.soi_size == 0) return;
+      const int64_t col = a.col0 + s;
+      for (int g = 0; g < ngl; g++) {
+        uint32_t v = kFull;
+        if (lane < a.soi_size) {
+          const uint32_t x = st[my_soi * gpb + g];
+          v = my_val ? x : ~x;
+        }
+        v = __reduce_and_sync(kFull, v);
+        if (lane == 0 && col >= 0) a.bits[(size_t)(g0 + g) * a.bits_cap + col] = v & lane_mask(a.omega, g0 + g);
+      }
+    };
+    if (producer)
+      for (int s = 0; s < kRing - 1; s++) issue_warp(s);
+    int ring_slot = 0;
+    for (int s = 0; s < a.steps; s++) {
+      if (producer) async_wait<kRing - 2>();
+      __syncthreads();
+      if (producer) {
+        if (s > 0) indicator_warp(cur, s - 1);
+        issue_warp(s + kRing - 1);
+      } else {
+        const uint32_t *w = ring + ring_slot * slot_words + woff;
+        const uint32_t P = active ? w[0] : 0u;
+        uint32_t rest = vmask & ~P;
+        uint32_t sel = L > 1 ? w[1] : (L == 1 ? rest : 0u);
+        rest &= ~sel;
+        uint32_t fword = sel & R.eval(0, cur, sub);
+        if (LW > 1) {
+          sel = L > 2 ? w[2] : (L == 2 ? rest : 0u);
+          rest &= ~sel;
+          fword |= sel & R.eval(1, cur, sub);
+          if (LW > kResident) eval_rest(kResident, LW, L, f0, gl, sub, w, rest, fword);
+        }
+        if (active && sub == 0) finish(idx, gl, P, fword, ring_any + ring_slot * gpbA);
+      }
+      ring_slot = ring_slot + 1 == kRing ? 0 : ring_slot + 1;
       uint32_t *tmp = cur;
       cur = nxt;
       nxt = tmp;
     }
+    if (producer) async_wait<0>();
+    __syncthreads();
+    if (producer) indicator_warp(cur, a.steps - 1);
   } else {
+    for (int s = 0; s < kRing - 1; s++) issue(s);
     for (int s = 0; s < a.steps; s++) {
       step_top(s);
       const uint32_t *slot = ring + (size_t)(s % kRing) * gpb * W;
@@ -385,10 +426,10 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
       cur = nxt;
       nxt = tmp;
     }
+    async_wait<0>();
+    __syncthreads();
+    indicator(cur, a.steps - 1);
   }
-  async_wait<0>();
-  __syncthreads();
-  indicator(cur, a.steps - 1);
   for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
     const int i = idx / gpb, gl = idx - i * gpb;
     if (gl < ngl) a.state[(size_t)(g0 + gl) * n + i] = cur[idx];
