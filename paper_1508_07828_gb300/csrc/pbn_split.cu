@@ -108,6 +108,11 @@ __device__ __forceinline__ void async_wait() {
 
 }  // namespace
 
+// Indicator words of the last kIndRing steps per group (register-resident
+// path): the threads of the state-of-interest nodes AND their part into the
+// word of their step; the producer warp stores them 32 steps at a time.
+constexpr int kIndRing = 64;
+
 // Ring slots of category words: RING - 1 steps are in flight ahead of the
 // step being applied (8, or 3 when 8 slots do not fit shared memory).
 size_t apply_smem_bytes(int n, int F, int gpb, int W, int staging, int ring) {
@@ -116,6 +121,7 @@ size_t apply_smem_bytes(int n, int F, int gpb, int W, int staging, int ring) {
   if (staging == STAGE_SMEM) b += (size_t)F * 16;
   b += ((size_t)n * 4 + 15) & ~(size_t)15;                 // node records
   b += 2 * (size_t)n * gpb * 4;                            // current and next state
+  b += (size_t)gpb * kIndRing * 4;                         // indicator words of recent steps
   return b;
 }
 
@@ -246,10 +252,12 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
   const int items = n * gpb;
   uint32_t *cur = reinterpret_cast<uint32_t *>(p);
   uint32_t *nxt = cur + items;
+  uint32_t *ind = nxt + items;  // [gpb][kIndRing]
   for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
     const int i = idx / gpb, gl = idx - i * gpb;
     cur[idx] = gl < ngl ? a.state[(size_t)(g0 + gl) * n + i] : 0u;
   }
+  for (int j = threadIdx.x; j < gpb * kIndRing; j += blockDim.x) ind[j] = kFull;
   __syncthreads();  // tables and state staged before any thread reads another's records
   // step s's words of this CTA's groups: one contiguous run of ngl * W words
   const int chunks16 = ngl * W / 4;
@@ -314,13 +322,16 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
       }
     }
   };
-  auto finish = [&](int idx, int gl, uint32_t P, uint32_t fword, const uint32_t *slot_any) {
+  auto finish = [&](int idx, int gl, uint32_t P, uint32_t fword, const uint32_t *slot_any) -> uint32_t {
+    uint32_t v;
     if (MODE == PBN_PERTURB_PER_NODE) {
-      nxt[idx] = (P & ~cur[idx]) | fword;
+      v = (P & ~cur[idx]) | fword;
     } else {
       const uint32_t any = slot_any[gl];
-      nxt[idx] = (any & (cur[idx] ^ P)) | (~any & fword);
+      v = (any & (cur[idx] ^ P)) | (~any & fword);
     }
+    nxt[idx] = v;
+    return v;
   };
   if (T > 1 && items * T <= (int)blockDim.x - 32) {
     // One item per T threads for the whole launch, everything that does not
@@ -356,17 +367,25 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
       }
       async_commit();
     };
-    auto indicator_warp = [&](const uint32_t *st, int s) {
+    // this item's part of the state of interest: the node must be 1 (need1)
+    // and/or 0 (need0; both when the state of interest names it twice)
+    bool need1 = false, need0 = false;
+    if (active && sub == 0)
+      for (int m = 0; m < a.soi_size; m++)
+        if ((int)a.soi_node[m] == node_id(rec)) ((a.soi_val >> m) & 1u ? need1 : need0) = true;
+    const bool in_soi = need1 || need0;
+    // store the indicator words of steps s0 .. s0+cnt-1 (complete) and make
+    // their ring words ready for reuse
+    auto flush = [&](int s0, int cnt) {
       if (a.soi_size == 0) return;
-      const int64_t col = a.col0 + s;
       for (int g = 0; g < ngl; g++) {
-        uint32_t v = kFull;
-        if (lane < a.soi_size) {
-          const uint32_t x = st[my_soi * gpb + g];
-          v = my_val ? x : ~x;
+        const int st = s0 + lane;
+        if (lane < cnt) {
+          uint32_t *word = ind + g * kIndRing + (st & (kIndRing - 1));
+          const int64_t col = a.col0 + st;
+          if (col >= 0) a.bits[(size_t)(g0 + g) * a.bits_cap + col] = *word & lane_mask(a.omega, g0 + g);
+          *word = kFull;
         }
-        v = __reduce_and_sync(kFull, v);
-        if (lane == 0 && col >= 0) a.bits[(size_t)(g0 + g) * a.bits_cap + col] = v & lane_mask(a.omega, g0 + g);
       }
     };
     if (producer)
@@ -376,7 +395,7 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
       if (producer) async_wait<kRing - 2>();
       __syncthreads();
       if (producer) {
-        if (s > 0) indicator_warp(cur, s - 1);
+        if (s > 0 && (s & 31) == 0) flush(s - 32, 32);  // steps s-32 .. s-1 are complete
         issue_warp(s + kRing - 1);
       } else {
         const uint32_t *w = ring + ring_slot * slot_words + woff;
@@ -391,7 +410,11 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
           fword |= sel & R.eval(1, cur, sub);
           if (LW > kResident) eval_rest(kResident, LW, L, f0, gl, sub, w, rest, fword);
         }
-        if (active && sub == 0) finish(idx, gl, P, fword, ring_any + ring_slot * gpbA);
+        if (active && sub == 0) {
+          const uint32_t v = finish(idx, gl, P, fword, ring_any + ring_slot * gpbA);
+          if (in_soi)
+            atomicAnd(ind + gl * kIndRing + (s & (kIndRing - 1)), (need1 ? v : kFull) & (need0 ? ~v : kFull));
+        }
       }
       ring_slot = ring_slot + 1 == kRing ? 0 : ring_slot + 1;
       uint32_t *tmp = cur;
@@ -400,7 +423,10 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
     }
     if (producer) async_wait<0>();
     __syncthreads();
-    if (producer) indicator_warp(cur, a.steps - 1);
+    if (producer) {
+      const int done = ((a.steps - 1) >> 5) << 5;  // steps already stored
+      flush(done, a.steps - done);
+    }
   } else {
     for (int s = 0; s < kRing - 1; s++) issue(s);
     for (int s = 0; s < a.steps; s++) {
