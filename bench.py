@@ -45,7 +45,7 @@ PSI0 = 1024
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -131,30 +131,39 @@ class ClockSampler:
 
 # -------------------------------------------------------------- roofline
 
-def algorithmic_ops_per_item(net) -> np.ndarray:
-    """Integer operations the bit-sliced step needs for one (node, chain
-    group) item, per node, in expectation:
+def draw_ops_per_item(net) -> np.ndarray:
+    """Integer operations of the category draw of one (node, chain group)
+    item, per node, in expectation:
       Philox4x32-10 blocks: 40 ops each (10 rounds x (2 wide multiplies +
         2 three-input XORs)); blocks needed so that no lane of 32 is still tied
         with one of the node's L category bounds: 1 + sum_b>=1 of
         1 - (1 - min(1, L 2^-4b))^32;
-      digit comparison: 3 ops per bound per digit (4 digits per block);
-      function evaluation for each function some lane selects (probability
-        1 - (1 - c)^32): 2 ops per truth-table leaf, 1 per multiplexer,
-        1 load per parent: 3 * 2^k - 1 + k;
-      combine and store: 2 ops."""
+      digit comparison: 3 ops per bound per digit (4 digits per block)."""
     ops = np.zeros(net.n)
     for i in range(net.n):
-        fs = list(net.functions_of(i))
-        L = len(fs)
+        L = len(list(net.functions_of(i)))
         blocks = 1.0 + sum(1.0 - (1.0 - min(1.0, L * 2.0 ** (-4 * b))) ** 32 for b in range(1, 8))
-        o = blocks * (40 + 4 * 3 * L) + 2
-        for f in fs:
+        ops[i] = blocks * (40 + 4 * 3 * L)
+    return ops
+
+
+def apply_ops_per_item(net) -> np.ndarray:
+    """Integer operations of the state update of one item, per node, in
+    expectation: for each function some lane selects (probability
+    1 - (1 - c)^32) 2 ops per truth-table leaf, 1 per multiplexer and 1 load
+    per parent (3 * 2^k - 1 + k); combine and store: 2 ops."""
+    ops = np.full(net.n, 2.0)
+    for i in range(net.n):
+        for f in net.functions_of(i):
             k = int(net.par_offset[f + 1] - net.par_offset[f])
             c = float(net.select_prob[f])
-            o += (1.0 - (1.0 - c) ** 32) * (3 * (1 << k) - 1 + k)
-        ops[i] = o
+            ops[i] += (1.0 - (1.0 - c) ** 32) * (3 * (1 << k) - 1 + k)
     return ops
+
+
+def algorithmic_ops_per_item(net) -> np.ndarray:
+    """Whole step: the draw plus the update (the fused kernel does both)."""
+    return draw_ops_per_item(net) + apply_ops_per_item(net)
 
 
 def alu_peak_tops(device_index):
@@ -215,9 +224,11 @@ def run_reference(args):
     net, soi, cfg = workload()
     omega = cfg["omega"]
     # one step = the oracle simulating all chains for a fixed number of
-    # transitions (about 4 s of CPU work)
+    # transitions: about 2 minutes of CPU work over the whole run, at most
+    # 4 s per step
+    per_step_s = min(4.0, 120.0 / max(args.steps, 1))
     _, calib_steps, _ = oracle_sample(net, soi, omega, target_s=0.5)
-    steps_per = max(2, calib_steps * 8)
+    steps_per = max(2, int(calib_steps * per_step_s / 0.5))
     st = oracle.init_states(net, 7, omega)
     t0 = 0
     for _ in range(args.warmup):
@@ -320,17 +331,29 @@ def run_ours(args):
         return
 
     value = upd_all / (total_ms / 1e3)
-    # roofline of the simulation kernel: algorithmic integer ops per launch
-    # over the event-timed launch durations of the timed region
-    ops_item = algorithmic_ops_per_item(net)
-    ops_per_group_step = float(ops_item.sum())
-    groups = (omega + 31) // 32
+    # roofline of the dominant simulation kernel: algorithmic integer ops per
+    # launch over its event-timed launch durations in the timed region.  The
+    # select-ahead schedule (chosen for this chain count) splits a step into
+    # select_kernel (category draws) and apply_kernel (state updates, the
+    # longer of the two); the fused schedule runs sim_kernel alone.
     sim_ms = sum(r["sim_ms"] for r in reports)
     sim_launches = sum(r["sim_launches"] for r in reports)
+    apply_ms = sum(r["apply_ms"] for r in reports)
+    apply_launches = sum(r["apply_launches"] for r in reports)
     items = sum(r["sim_items"] for r in reports)
-    ops = ops_per_group_step * items / net.n
-    achieved = ops / (sim_ms / 1e3) / 1e12
+    groups_steps = items / net.n
     peak, sms, mhz, peak_src = alu_peak_tops(local)
+    if apply_launches:
+        kernel, k_ms, k_launches = "apply_kernel", apply_ms, apply_launches
+        ops_per_group_step = float(apply_ops_per_item(net).sum())
+        other = {"select_kernel": {"achieved": float(draw_ops_per_item(net).sum()) * groups_steps /
+                                   ((sim_ms - apply_ms) / 1e3) / 1e12, "ms": sim_ms - apply_ms,
+                                   "launches": sim_launches - apply_launches}}
+    else:
+        kernel, k_ms, k_launches = "sim_kernel", sim_ms, sim_launches
+        ops_per_group_step = float(algorithmic_ops_per_item(net).sum())
+        other = {}
+    achieved = ops_per_group_step * groups_steps / (k_ms / 1e3) / 1e12
     lat = sorted(times)
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -339,12 +362,14 @@ def run_ours(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(np.mean(lat))},
             "queries_per_s": args.steps * world / (total_ms / 1e3),
-            "roofline": {"bound": "alu", "kernel": "sim_kernel", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
                          "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
                          "peak_source": f"issue rate {sms} SMs x 128 lanes x {mhz:.0f} MHz ({peak_src})",
-                         "sim_share_of_step": sim_ms / total_ms,
+                         "kernel_share_of_step": k_ms / total_ms, "sim_share_of_step": sim_ms / total_ms,
                          "ops_per_update": ops_per_group_step / net.n / 32,
-                         "launches": sim_launches, "avg_launch_ms": sim_ms / max(sim_launches, 1)},
+                         "launches": k_launches, "avg_launch_ms": k_ms / max(k_launches, 1),
+                         "ns_per_transition": 1e6 * sim_ms / max(groups_steps / ((omega + 31) // 32), 1),
+                         "other_kernels": other},
             "clocks": clk,
             "e2e": {"value": e2e_upd_all / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": e2e_d2h // max(args.steps, 1)},

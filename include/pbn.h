@@ -129,8 +129,9 @@ typedef struct pbn_run_cfg {
  * where the fused step waits on its Philox rounds with most SMs idle.
  * SELECT_AHEAD takes staging 0, 1 or 3 and needs device scratch of up to
  * 64 MiB per stream (kept by the library, grown on demand).  AUTO: select-ahead
- * when the chain groups (ceil(omega / 32)) number at most the SMs and its
- * shared memory fits, else fused. */
+ * when the chain groups (ceil(omega / 32)) number at most the SMs, the network
+ * has at most 1000 nodes or the groups at most half the SMs, and its shared
+ * memory fits; else fused. */
 enum { PBN_SCHEDULE_AUTO = 0, PBN_SCHEDULE_FUSED = 1, PBN_SCHEDULE_SELECT_AHEAD = 2 };
 
 /* ---------------------------------------------------------------- network */
@@ -269,6 +270,8 @@ typedef struct pbn_two_state_report {
     int64_t kernel_launches;      /* all kernel launches of the query */
     int64_t sim_items;            /* (node, chain group, transition) items simulated */
     int64_t d2h_bytes;            /* device -> host bytes read for the stopping decisions */
+    double apply_ms;              /* select-ahead schedule: CUDA-event time of the apply launches alone */
+    int64_t apply_launches;       /* select-ahead schedule: apply launches (0 under the fused schedule) */
 } pbn_two_state_report;
 
 /* Alg. GR then Alg. 3 (Sec. 4.2) end to end on the device: chains are
@@ -300,6 +303,8 @@ typedef struct pbn_skart_report {
     double device_ms;
     double sim_ms;
     int64_t sim_launches, kernel_launches, sim_items, d2h_bytes;
+    double apply_ms;
+    int64_t apply_launches;
 } pbn_skart_report;
 
 /* Alg. GR then Alg. 4 (Sec. 4.3) end to end on the device.  Synchronises

@@ -96,7 +96,8 @@ class TwoStateReport(ctypes.Structure):
                 ("gr_psi", c_i64), ("length", c_i64), ("sample_size", c_i64), ("M", c_i64), ("N", c_i64),
                 ("ones", c_i64), ("n4", c_i64 * 4), ("gr_rounds", c_i32), ("ts_rounds", c_i32),
                 ("chain_node_updates", c_i64), ("device_ms", c_dbl), ("sim_ms", c_dbl), ("sim_launches", c_i64),
-                ("kernel_launches", c_i64), ("sim_items", c_i64), ("d2h_bytes", c_i64)]
+                ("kernel_launches", c_i64), ("sim_items", c_i64), ("d2h_bytes", c_i64), ("apply_ms", c_dbl),
+                ("apply_launches", c_i64)]
 
 
 class SkartQuery(ctypes.Structure):
@@ -110,7 +111,8 @@ class SkartReport(ctypes.Structure):
                [(k, c_i64) for k in ("psi", "length", "kappa", "batches", "spacer", "sample_size")] + \
                [("gr_rounds", c_i32), ("rand_rounds", c_i32), ("ci_rounds", c_i32),
                 ("chain_node_updates", c_i64), ("device_ms", c_dbl), ("sim_ms", c_dbl), ("sim_launches", c_i64),
-                ("kernel_launches", c_i64), ("sim_items", c_i64), ("d2h_bytes", c_i64)]
+                ("kernel_launches", c_i64), ("sim_items", c_i64), ("d2h_bytes", c_i64), ("apply_ms", c_dbl),
+                ("apply_launches", c_i64)]
 
 
 class EngineCfg(ctypes.Structure):

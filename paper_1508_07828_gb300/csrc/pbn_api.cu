@@ -263,9 +263,12 @@ int plan_select(const pbn::NetDev &net, int64_t omega, int gpb_req, int threads_
       return fail(PBN_ERR_UNSUPPORTED, "select-ahead shared memory does not fit (n %d, F %d)", net.n, net.F);
     gpb = std::max(1, gpb / 2);
   }
-  // 4 threads share an item's truth tables unless asked otherwise: the step is
-  // a chain of dependent operations, so spreading it over more warps pays
-  const int T = T_req > 0 ? T_req : 4;
+  // Threads per item unless asked: 2 while the items of a CTA are few enough
+  // for the register-resident path (the step is a chain of dependent
+  // operations, so spreading it over more warps pays), 1 beyond (there extra
+  // threads only multiply the work of the generic path).  Measured on GB300
+  // over n = 100 .. 3000 with 256 .. 4096 chains.
+  const int T = T_req > 0 ? T_req : (net.n * gpb <= 300 ? 2 : 1);
   if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
   const int items = net.n * gpb;
   const int tmax = pbn::apply_threads_limit(T);
@@ -283,8 +286,16 @@ int plan_select(const pbn::NetDev &net, int64_t omega, int gpb_req, int threads_
   return PBN_OK;
 }
 
+// Optional CUDA-event timing of the apply launches (the dominant kernel of the
+// select-ahead schedule): `next` hands out events from the caller's pool.
+struct ApplyTiming {
+  cudaEvent_t (*next)(void *ctx) = nullptr;
+  void *ctx = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs;
+};
+
 int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, bool record,
-                     const SelectPlan &sp, cudaStream_t s, int64_t *launches) {
+                     const SelectPlan &sp, cudaStream_t s, int64_t *launches, ApplyTiming *timing) {
   const int G = (int)((ch.omega + 31) / 32);
   const int64_t per_step = (int64_t)G * sp.W * 4;
   const int64_t C = std::max<int64_t>(1, std::min(kSelectMaxSteps, kSelectBudgetBytes / per_step));
@@ -317,7 +328,18 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
     if (cfg.perturb_mode == PBN_PERTURB_GLOBAL)
       CUDA_TRY(cudaMemsetAsync(sc->anyw, 0, (size_t)k * G * 4, s), "select-ahead clear");
     CUDA_TRY(pbn::launch_select(a, cfg.perturb_mode, 1, s), "select launch");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timing) {
+      e0 = timing->next(timing->ctx);
+      e1 = timing->next(timing->ctx);
+      if (!e0 || !e1) return fail(PBN_ERR_CUDA, "event creation failed");
+      CUDA_TRY(cudaEventRecord(e0, s), "event");
+    }
     CUDA_TRY(pbn::launch_apply(a, cfg.perturb_mode, sp.ring, sp.T, sp.threads, sp.smem, s), "apply launch");
+    if (timing) {
+      CUDA_TRY(cudaEventRecord(e1, s), "event");
+      timing->pairs.emplace_back(e0, e1);
+    }
     ch.length += k;
     if (launches) *launches += 2;
   }
@@ -325,7 +347,7 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
 }
 
 int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, cudaStream_t s,
-              int64_t *launches = nullptr) {
+              int64_t *launches = nullptr, ApplyTiming *timing = nullptr) {
   if (steps < 0) return fail(PBN_ERR_INVALID, "negative step count");
   if (steps == 0) return PBN_OK;
   const bool record = ch.bits && ch.bits_cap > 0 && cfg.soi.size > 0;
@@ -340,15 +362,19 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
     return fail(PBN_ERR_INVALID, "schedule %d", cfg.schedule);
   if (!pbn::device_status()) return fail(PBN_ERR_CUDA, "device status word unavailable");
   const int G = (int)((ch.omega + 31) / 32);
+  // automatic: select-ahead while one CTA per chain group leaves SMs idle,
+  // except for large networks with groups for more than half the SMs, where
+  // the fused kernel's per-step work is already spread well (measured)
   const bool want_select = cfg.schedule == PBN_SCHEDULE_SELECT_AHEAD ||
-                           (cfg.schedule == PBN_SCHEDULE_AUTO && G <= sm_count() && cfg.staging != 2 &&
+                           (cfg.schedule == PBN_SCHEDULE_AUTO && G <= sm_count() &&
+                            (net.n <= 1000 || 2 * G <= sm_count()) && cfg.staging != 2 &&
                             cfg.threads_per_item == 0 && cfg.blocks_per_round == 0);
   if (want_select) {
     SelectPlan sp;
     const std::string saved = g_err;
     int rc = plan_select(net, ch.omega, cfg.groups_per_block, cfg.threads_per_block, cfg.threads_per_item,
                          cfg.staging, &sp);
-    if (rc == PBN_OK) return run_select_ahead(net, cfg, ch, steps, record, sp, s, launches);
+    if (rc == PBN_OK) return run_select_ahead(net, cfg, ch, steps, record, sp, s, launches, timing);
     if (cfg.schedule == PBN_SCHEDULE_SELECT_AHEAD) return rc;
     g_err = saved;  // automatic choice: fall back to the fused schedule
   }
@@ -687,6 +713,7 @@ struct Query {
   void *d_res = nullptr;
   size_t n_events = 0;   // events 0, 1: whole query; then start/stop pairs of simulation launches
   int64_t sim_launches = 0, kernel_launches = 0, sim_items = 0, d2h_bytes = 0;
+  ApplyTiming apply_timing;
 
   Query(const pbn::NetDev &n, cudaStream_t st)
       : net(n), s(st), ws(workspace_for(st)), hold(ws.mu), sc(ws.sc) {
@@ -749,9 +776,12 @@ struct Query {
     cudaEvent_t a = ws.event(n_events), b = ws.event(n_events + 1);
     if (!a || !b) return fail(PBN_ERR_CUDA, "event creation failed");
     n_events += 2;
+    sim_pairs.emplace_back(a, b);
+    apply_timing.next = &Query::next_event;
+    apply_timing.ctx = this;
     CUDA_TRY(cudaEventRecord(a, s), "event");
     int64_t launches = 0;
-    rc = run_steps(net, cfg, ch, steps, s, &launches);
+    rc = run_steps(net, cfg, ch, steps, s, &launches, &apply_timing);
     if (rc) return rc;
     CUDA_TRY(cudaEventRecord(b, s), "event");
     sim_launches += launches;
@@ -813,14 +843,31 @@ struct Query {
     return ms;
   }
 
+  // events 2.. hold (start, stop) pairs around each run of steps; the apply
+  // launches' pairs are drawn from the same pool, so the two sets are kept apart
   double sim_ms() {
     double total = 0.0;
-    for (size_t k = 2; k + 1 < n_events; k += 2) {
+    for (const auto &pr : sim_pairs) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ws.events[k], ws.events[k + 1]) == cudaSuccess) total += ms;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) total += ms;
     }
     return total;
   }
+
+  double apply_ms() {
+    double total = 0.0;
+    for (const auto &pr : apply_timing.pairs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) total += ms;
+    }
+    return total;
+  }
+
+  static cudaEvent_t next_event(void *ctx) {
+    Query *q = static_cast<Query *>(ctx);
+    return q->ws.event(q->n_events++);
+  }
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sim_pairs;
 };
 
 int check_query_common(const pbn_net *net, int64_t omega, int64_t psi0, double thr, int64_t max_length,
@@ -903,6 +950,8 @@ extern "C" int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_qu
   out->device_ms = Q.elapsed_ms();
   out->sim_ms = Q.sim_ms();
   out->sim_launches = Q.sim_launches;
+  out->apply_ms = Q.apply_ms();
+  out->apply_launches = (int64_t)Q.apply_timing.pairs.size();
   out->kernel_launches = Q.kernel_launches;
   out->sim_items = Q.sim_items;
   out->d2h_bytes = Q.d2h_bytes;
@@ -997,6 +1046,8 @@ extern "C" int pbn_estimate_skart(const pbn_net *net, const pbn_skart_query *q, 
   out->device_ms = Q.elapsed_ms();
   out->sim_ms = Q.sim_ms();
   out->sim_launches = Q.sim_launches;
+  out->apply_ms = Q.apply_ms();
+  out->apply_launches = (int64_t)Q.apply_timing.pairs.size();
   out->kernel_launches = Q.kernel_launches;
   out->sim_items = Q.sim_items;
   out->d2h_bytes = Q.d2h_bytes;

@@ -62,13 +62,15 @@ STRUCTS = {
     "TwoStateReport": ("pbn_two_state_report", ["prob", "rhat", "alpha", "beta", "psi", "gr_psi", "length",
                                                 "sample_size", "M", "N", "ones", "n4", "gr_rounds", "ts_rounds",
                                                 "chain_node_updates", "device_ms", "sim_ms", "sim_launches",
-                                                "kernel_launches", "sim_items", "d2h_bytes"]),
+                                                "kernel_launches", "sim_items", "d2h_bytes", "apply_ms",
+                                                "apply_launches"]),
     "SkartQuery": ("pbn_skart_query", ["omega", "psi0", "rhat_threshold", "H_star", "relative", "alpha",
                                        "max_length", "seed", "perturb_mode", "soi"]),
     "SkartReport": ("pbn_skart_report", ["mean", "ci_lo", "ci_hi", "H", "var", "skew", "phi", "rhat", "psi",
                                          "length", "kappa", "batches", "spacer", "sample_size", "gr_rounds",
                                          "rand_rounds", "ci_rounds", "chain_node_updates", "device_ms", "sim_ms",
-                                         "sim_launches", "kernel_launches", "sim_items", "d2h_bytes"]),
+                                         "sim_launches", "kernel_launches", "sim_items", "d2h_bytes", "apply_ms",
+                                         "apply_launches"]),
     "EngineCfg": ("pbn_engine_cfg", ["hbm_budget_bytes", "max_active", "steps_per_epoch", "threads_per_block",
                                      "items_per_thread", "use_graph"]),
     "EngineQuery": ("pbn_engine_query", ["net", "method", "two_state", "skart", "tag"]),
