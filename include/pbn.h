@@ -59,7 +59,8 @@ enum { PBN_PERTURB_PER_NODE = 0, PBN_PERTURB_GLOBAL = 1 };
 #define PBN_MAX_NODES 4096          /* node ids are 12-bit in the device tables */
 #define PBN_MAX_PARENTS 5           /* truth tables are one 32-bit word */
 #define PBN_MAX_FUNCTIONS_PER_NODE 8
-#define PBN_MAX_SOI 32
+#define PBN_MAX_SOI 32               /* state-of-interest entries of one run, over all its properties */
+#define PBN_MAX_PROPERTIES 8         /* properties abstracted from one set of trajectories (Sec. 4.2) */
 
 /*
  * A PBN G(V,F) (Sec. 2.2) with perturbation probability p, in CSR form.  All
@@ -120,6 +121,13 @@ typedef struct pbn_run_cfg {
                                    from global memory through L1), 1 = whole tables in shared memory,
                                    2 = TMA tiles streamed through shared memory, 3 = global */
     int32_t schedule;           /* PBN_SCHEDULE_*: how the steps are laid on the GPU (same chains either way) */
+    /* Several properties recorded in one pass (Sec. 4.2, last part): when
+     * n_props > 0, props[0 .. n_props-1] replace `soi` (each non-empty; at most
+     * PBN_MAX_PROPERTIES, PBN_MAX_SOI entries in total) and chains->bits holds
+     * n_props bitstreams one after the other, property m at
+     * bits + m * ceil(omega/32) * bits_cap. */
+    int32_t n_props;
+    const pbn_soi *props;
 } pbn_run_cfg;
 
 /* Schedules of pbn_run_chains.  FUSED: one kernel draws each item's category
@@ -281,6 +289,29 @@ typedef struct pbn_two_state_report {
  * Errors: PBN_ERR_NOT_CONVERGED (max_length), PBN_ERR_INVALID, PBN_ERR_OOM, PBN_ERR_CUDA. */
 int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_query *q, pbn_two_state_report *out,
                            void *stream);
+
+/* One property's part of a multi-property query (Sec. 4.2, last part). */
+typedef struct pbn_property_result {
+    double prob, alpha, beta;
+    double rhat;            /* its R-hat at the accepted Gelman-Rubin psi */
+    int64_t M, N, ones;
+    int64_t n4[4];
+} pbn_property_result;
+
+/* Several properties (sets of states of interest) from the same trajectories
+ * (Sec. 4.2, last part): one set of chains, each property abstracted from it
+ * in the same simulation pass.  Alg. GR doubles psi until every property's
+ * R-hat is below the threshold; each round estimates alpha, beta, M, N per
+ * property; the chains grow by the smallest deficit among the properties
+ * whose N exceeds the merged sample, until none does; the burn-in check
+ * takes the largest M.  One property gives exactly pbn_estimate_two_state.
+ * q->soi is ignored; props[0 .. n_props-1] (1 <= n_props <= PBN_MAX_PROPERTIES,
+ * at most PBN_MAX_SOI entries in total) name the properties; each[m] receives
+ * property m's result and `out` the common fields (its per-property fields
+ * repeat property 0).  Synchronises `stream`.  Errors as pbn_estimate_two_state. */
+int pbn_estimate_two_state_multi(const pbn_net *net, const pbn_two_state_query *q, int32_t n_props,
+                                 const pbn_soi *props, pbn_two_state_report *out, pbn_property_result *each,
+                                 void *stream);
 
 typedef struct pbn_skart_query {
     int64_t omega;

@@ -19,6 +19,10 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
   norm_ppf, t_ppf    scipy.stats norm.ppf / t.ppf
   skewness           scipy.stats.skew
   estimate_two_state exact answers on small networks (within r)
+  estimate_two_state_multi
+                     reduces to estimate_two_state for one property and for
+                     repeated copies of it; complementary properties sum to 1
+                     exactly; exact answers on small networks (within r)
   estimate_skart     coverage on processes with a known mean; its constants
                      (skewness threshold, test size, spacer limit, growth
                      factors) are placeholders: parity unpinned.
@@ -109,6 +113,7 @@ def lib():
             L.orc_two_state_MN.argtypes = [dbl, dbl, dbl, dbl, dbl, vp, vp]
             L.orc_transition_counts.argtypes = [vp, i64, i64, i64, i64, vp]
             L.orc_estimate_two_state.argtypes = [vp, vp, vp, i32, vp]
+            L.orc_estimate_two_state_multi.argtypes = [vp, i32, vp, vp, vp, vp, vp]
             L.orc_skewness.argtypes = [vp, i64]; L.orc_skewness.restype = dbl
             L.orc_vonneumann_pass.argtypes = [vp, i64, i64, i64, dbl, vp]
             L.orc_skart_ci_from_means.argtypes = [vp, i64, i64, dbl, vp]
@@ -259,6 +264,40 @@ def estimate_two_state(net, soi, omega, seed, psi0=1024, rhat=1.05, eps=1e-10, r
     out = {k: getattr(run, k) for k, _ in _TwoStateRun._fields_ if k != "n4"}
     out["n4"] = list(run.n4)
     out["status"] = rc
+    return out
+
+
+class _Property(ctypes.Structure):
+    _fields_ = [("prob", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("rhat", ctypes.c_double), ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("ones", ctypes.c_int64),
+                ("n4", ctypes.c_int64 * 4)]
+
+
+MAX_PROPERTIES = 8
+
+
+def estimate_two_state_multi(net, sois, omega, seed, psi0=1024, rhat=1.05, eps=1e-10, r=0.005, s=0.95,
+                             mode=PER_NODE, max_length=1 << 26) -> dict:
+    """Several properties from the same trajectories (Sec. 4.2, last part):
+    common chains, Alg. GR over every property, extension by the smallest
+    deficit, burn-in by the largest M.  Returns the common run fields (whose
+    per-property fields repeat property 0) and "properties": one dict each."""
+    h = NetHandle(net)
+    q = len(sois)
+    nodes = np.ascontiguousarray(np.concatenate([np.asarray(x.nodes) for x in sois]), dtype=np.int32)
+    vals = np.ascontiguousarray(np.concatenate([np.asarray(x.values) for x in sois]), dtype=np.uint8)
+    sizes = np.ascontiguousarray([len(x.nodes) for x in sois], dtype=np.int32)
+    run = _TwoStateRun()
+    run.omega, run.psi0, run.rhat_threshold, run.max_length = omega, psi0, rhat, max_length
+    run.mode, run.seed, run.eps, run.r, run.s = mode, seed, eps, r, s
+    props = (_Property * MAX_PROPERTIES)()
+    rc = lib().orc_estimate_two_state_multi(h.ref, q, _ptr(nodes), _ptr(vals), _ptr(sizes), ctypes.byref(run),
+                                            ctypes.byref(props))
+    out = {k: getattr(run, k) for k, _ in _TwoStateRun._fields_ if k != "n4"}
+    out["n4"] = list(run.n4)
+    out["status"] = rc
+    out["properties"] = [dict({k: getattr(props[m], k) for k, _ in _Property._fields_ if k != "n4"},
+                              n4=list(props[m].n4)) for m in range(q)]
     return out
 
 

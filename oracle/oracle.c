@@ -549,6 +549,141 @@ done:
 }
 
 /* ------------------------------------------------------------------------- */
+/* Several properties from the same trajectories (Sec. 4.2, last part).        */
+/* ------------------------------------------------------------------------- */
+
+#define ORC_MAX_PROPERTIES 8
+
+typedef struct {
+    double prob, alpha, beta, rhat;
+    int64_t M, N, ones;
+    int64_t n4[4];
+} orc_property;
+
+/*
+ * q properties (sets of states of interest) share one set of chains; every
+ * property abstracts the same trajectories into its own meta-state sequence.
+ * Here the sharing is literal: q chain sets opened with the same seed follow
+ * the same trajectories (counter-based randomness) and differ only in the
+ * property they record.  Read as follows where the text is silent:
+ *  - Alg. GR holds for every property: psi doubles until each property's
+ *    R-hat is below the threshold (run->rhat: the largest);
+ *  - in each round alpha, beta, M, N are computed per property; the chains
+ *    are extended by the smallest deficit among the properties whose N is
+ *    larger than the merged sample (the text: the next extension follows the
+ *    smallest N), until no N is larger than the sample;
+ *  - the burn-in check takes the largest M: if it exceeds psi, psi := that M
+ *    and the rounds repeat for every property;
+ *  - each property's estimate is its fraction of ones in the common final
+ *    window.
+ * With q = 1 every step is Alg. 3's.  run's per-property fields (prob, alpha,
+ * beta, M, N, n4, ones) repeat property 0.
+ */
+int orc_estimate_two_state_multi(const orc_net *net, int32_t q, const int32_t *soi_nodes,
+                                 const uint8_t *soi_values, const int32_t *soi_sizes, orc_two_state_run *run,
+                                 orc_property *props) {
+    if (q < 1 || q > ORC_MAX_PROPERTIES) return ORC_ERR_INVALID;
+    chains_t ch[ORC_MAX_PROPERTIES];
+    int rc = ORC_OK, opened = 0;
+    int64_t off = 0;
+    for (int m = 0; m < q; m++) {
+        rc = chains_open(&ch[m], net, run->mode, run->seed, run->omega, soi_nodes + off, soi_values + off,
+                         soi_sizes[m]);
+        if (rc) goto done;
+        opened++;
+        off += soi_sizes[m];
+    }
+    int64_t omega = run->omega;
+    /* Alg. GR over every property */
+    int64_t psi = run->psi0;
+    run->gr_rounds = 0;
+    for (;;) {
+        if (2 * psi > run->max_length) { rc = ORC_ERR_NOT_CONVERGED; goto done; }
+        for (int m = 0; m < q; m++)
+            if ((rc = chains_extend_to(&ch[m], 2 * psi))) goto done;
+        run->gr_rounds++;
+        int all = 1;
+        double worst = -INFINITY;
+        for (int m = 0; m < q; m++) {
+            double R = orc_gelman_rubin(ch[m].x, omega, ch[m].cap, psi, psi);
+            props[m].rhat = R;
+            if (!(R < run->rhat_threshold)) all = 0;
+            if (!(R <= worst)) worst = R;   /* NaN or larger */
+        }
+        run->rhat = worst;
+        if (all) break;
+        psi *= 2;
+    }
+    run->gr_psi = psi;
+    run->ts_rounds = 0;
+    for (;;) {                        /* burn-in check */
+        for (;;) {                    /* sample-size check */
+            int64_t L = ch[0].L, n = L - psi;
+            if (n < 2) {
+                if (psi + 2 > run->max_length) { rc = ORC_ERR_NOT_CONVERGED; goto done; }
+                for (int m = 0; m < q; m++)
+                    if ((rc = chains_extend_to(&ch[m], psi + 2))) goto done;
+                continue;
+            }
+            run->ts_rounds++;
+            int insufficient = 0;
+            for (int m = 0; m < q; m++) {
+                int64_t *c = props[m].n4;
+                orc_transition_counts(ch[m].x, omega, ch[m].cap, psi, n, c);
+                if (c[1] == 0 || c[2] == 0 || (c[0] + c[1]) == 0 || (c[2] + c[3]) == 0) insufficient = 1;
+            }
+            if (insufficient) {
+                if (L + n > run->max_length) { rc = ORC_ERR_NOT_CONVERGED; goto done; }
+                for (int m = 0; m < q; m++)
+                    if ((rc = chains_extend_to(&ch[m], L + n))) goto done;
+                continue;
+            }
+            int64_t smallest = -1;
+            for (int m = 0; m < q; m++) {
+                const int64_t *c = props[m].n4;
+                double a = (double)c[1] / (double)(c[0] + c[1]);
+                double b = (double)c[2] / (double)(c[2] + c[3]);
+                int64_t M, N;
+                if ((rc = orc_two_state_MN(a, b, run->eps, run->r, run->s, &M, &N))) goto done;
+                props[m].alpha = a; props[m].beta = b; props[m].M = M; props[m].N = N;
+                int64_t deficit = N - omega * n;
+                if (deficit > 0 && (smallest < 0 || deficit < smallest)) smallest = deficit;
+            }
+            if (smallest < 0) break;
+            int64_t extend_by = (smallest + omega - 1) / omega;
+            if (L + extend_by > run->max_length) { rc = ORC_ERR_NOT_CONVERGED; goto done; }
+            for (int m = 0; m < q; m++)
+                if ((rc = chains_extend_to(&ch[m], L + extend_by))) goto done;
+        }
+        int64_t Mmax = props[0].M;
+        for (int m = 1; m < q; m++)
+            if (props[m].M > Mmax) Mmax = props[m].M;
+        if (Mmax > psi) { psi = Mmax; continue; }
+        break;
+    }
+    {
+        int64_t L = ch[0].L, n = L - psi;
+        for (int m = 0; m < q; m++) {
+            int64_t ones = 0;
+            for (int64_t c = 0; c < omega; c++)
+                for (int64_t j = 0; j < n; j++) ones += ch[m].x[c * ch[m].cap + psi + j];
+            props[m].ones = ones;
+            props[m].prob = (double)ones / (double)(omega * n);
+        }
+        run->psi = psi;
+        run->length = L;
+        run->sample_size = omega * n;
+        run->prob = props[0].prob; run->alpha = props[0].alpha; run->beta = props[0].beta;
+        run->M = props[0].M; run->N = props[0].N; run->ones = props[0].ones;
+        memcpy(run->n4, props[0].n4, sizeof(run->n4));
+    }
+done:
+    run->status = rc;
+    for (int m = 0; m < opened; m++) chains_close(&ch[m]);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Skart pieces (Sec. 3.2, Alg. 2; parallel Alg. 4).                           */
 /* ------------------------------------------------------------------------- */
 

@@ -67,7 +67,7 @@ class Chains(ctypes.Structure):
 class RunCfg(ctypes.Structure):
     _fields_ = [("seed", c_u64), ("perturb_mode", c_i32), ("soi", Soi), ("groups_per_block", c_i32),
                 ("threads_per_block", c_i32), ("threads_per_item", c_i32), ("blocks_per_round", c_i32),
-                ("staging", c_i32), ("schedule", c_i32)]
+                ("staging", c_i32), ("schedule", c_i32), ("n_props", c_i32), ("props", c_vp)]
 
 
 class GrResult(ctypes.Structure):
@@ -98,6 +98,11 @@ class TwoStateReport(ctypes.Structure):
                 ("chain_node_updates", c_i64), ("device_ms", c_dbl), ("sim_ms", c_dbl), ("sim_launches", c_i64),
                 ("kernel_launches", c_i64), ("sim_items", c_i64), ("d2h_bytes", c_i64), ("apply_ms", c_dbl),
                 ("apply_launches", c_i64)]
+
+
+class PropertyResult(ctypes.Structure):
+    _fields_ = [("prob", c_dbl), ("alpha", c_dbl), ("beta", c_dbl), ("rhat", c_dbl), ("M", c_i64), ("N", c_i64),
+                ("ones", c_i64), ("n4", c_i64 * 4)]
 
 
 class SkartQuery(ctypes.Structure):
@@ -163,6 +168,8 @@ def lib():
             L.pbn_skart.argtypes = [P(Chains), c_i64, c_i64, c_i64, c_i64, c_dbl, c_dbl, c_vp, c_vp]
             L.pbn_skart_static.argtypes = [P(Chains), c_i64, c_i64, c_i64, c_i64, c_dbl, c_dbl, c_vp, c_vp]
             L.pbn_estimate_two_state.argtypes = [c_vp, P(TwoStateQuery), P(TwoStateReport), c_vp]
+            L.pbn_estimate_two_state_multi.argtypes = [c_vp, P(TwoStateQuery), c_i32, c_vp, P(TwoStateReport),
+                                                       P(PropertyResult), c_vp]
             L.pbn_estimate_skart.argtypes = [c_vp, P(SkartQuery), P(SkartReport), c_vp]
             L.pbn_engine_create.argtypes = [P(EngineCfg), c_vp, P(c_vp)]
             L.pbn_engine_destroy.argtypes = [c_vp]
@@ -271,19 +278,32 @@ class SoiArg:
         self.struct = Soi(self.size, self.nodes.ctypes.data, self.values.ctypes.data)
 
 
+class PropsArg:
+    """Several states of interest as a pbn_soi array (keeps the host arrays alive)."""
+
+    def __init__(self, sois):
+        self.items = [SoiArg(x) for x in (sois or [])]
+        self.array = (Soi * max(1, len(self.items)))(*[x.struct for x in self.items])
+        self.count = len(self.items)
+        self.ptr = ctypes.cast(self.array, c_vp).value if self.count else None
+
+
 # ------------------------------------------------------------------- chains
 
 class ChainSet:
     """omega chains of one network in caller-owned device memory (torch
-    tensors): bit-sliced states [G, n] and an indicator bitstream [G, cap]."""
+    tensors): bit-sliced states [G, n] and indicator bitstreams
+    [n_props * G, cap] (property m in rows m*G .. m*G+G-1)."""
 
-    def __init__(self, network: Network, omega: int, bits_cap: int = 0, bits_base: int = 0):
+    def __init__(self, network: Network, omega: int, bits_cap: int = 0, bits_base: int = 0, n_props: int = 1):
         torch = _torch()
         self.network = network
         self.omega = int(omega)
         self.G = (self.omega + 31) // 32
+        self.n_props = int(n_props)
         self.state = torch.zeros((self.G, network.n), dtype=torch.int32, device="cuda")
-        self.bits = torch.zeros((self.G, max(bits_cap, 1)), dtype=torch.int32, device="cuda") if bits_cap else None
+        self.bits = torch.zeros((self.n_props * self.G, max(bits_cap, 1)), dtype=torch.int32,
+                                device="cuda") if bits_cap else None
         self.c = Chains(self.omega, self.state.data_ptr(), self.bits.data_ptr() if self.bits is not None else None,
                         int(bits_cap), int(bits_base), 0)
 
@@ -307,10 +327,11 @@ class ChainSet:
         w = (st << np.arange(32, dtype=np.uint64)[None, :, None]).sum(axis=1).astype(np.uint32)
         self.state.copy_(torch.from_numpy(w.view(np.int32)))
 
-    def indicator_numpy(self, start: int, length: int) -> np.ndarray:
-        """Indicator bits uint8 [omega, length] of positions start .. start+length-1."""
+    def indicator_numpy(self, start: int, length: int, prop: int = 0) -> np.ndarray:
+        """Indicator bits uint8 [omega, length] of property `prop` at positions
+        start .. start+length-1."""
         col = start - int(self.c.bits_base)
-        w = self.bits[:, col:col + length].cpu().numpy().view(np.uint32)
+        w = self.bits[prop * self.G:(prop + 1) * self.G, col:col + length].cpu().numpy().view(np.uint32)
         lanes = np.arange(32, dtype=np.uint32)
         b = ((w[:, None, :] >> lanes[None, :, None]) & 1).astype(np.uint8)  # [G, 32, len]
         return b.reshape(self.G * 32, length)[: self.omega]
@@ -321,9 +342,10 @@ SCHEDULE = {"auto": 0, "fused": 1, "select_ahead": 2}
 
 
 def _cfg(seed, mode, soi_arg, groups_per_block=0, threads_per_block=0, threads_per_item=0, blocks_per_round=0,
-         staging="auto", schedule="auto"):
+         staging="auto", schedule="auto", props_arg=None):
     return RunCfg(int(seed), int(mode), soi_arg.struct, int(groups_per_block), int(threads_per_block),
-                  int(threads_per_item), int(blocks_per_round), STAGING[staging], SCHEDULE[schedule])
+                  int(threads_per_item), int(blocks_per_round), STAGING[staging], SCHEDULE[schedule],
+                  props_arg.count if props_arg else 0, props_arg.ptr if props_arg else None)
 
 
 def pbn_take_device_status() -> int:
@@ -341,10 +363,17 @@ def pbn_init_chains(chains: ChainSet, seed: int, mode: int = PER_NODE, stream=No
 
 def pbn_run_chains(chains: ChainSet, steps: int, seed: int, mode: int = PER_NODE, soi=None,
                    groups_per_block: int = 0, threads_per_block: int = 0, threads_per_item: int = 0,
-                   blocks_per_round: int = 0, staging: str = "auto", schedule: str = "auto", stream=None):
+                   blocks_per_round: int = 0, staging: str = "auto", schedule: str = "auto", props=None,
+                   stream=None):
+    """Extend every chain by `steps` transitions, recording the indicator of
+    `soi`, or of each of `props` (a list of states of interest, one bitstream
+    each: chains.n_props must match)."""
     soi_arg = SoiArg(soi)
+    props_arg = PropsArg(props) if props else None
+    if props_arg and props_arg.count != chains.n_props:
+        raise ValueError(f"{props_arg.count} properties for a chain set with {chains.n_props} bitstreams")
     cfg = _cfg(seed, mode, soi_arg, groups_per_block, threads_per_block, threads_per_item, blocks_per_round, staging,
-               schedule)
+               schedule, props_arg)
     _check(lib().pbn_run_chains(chains.network.handle, ctypes.byref(cfg), ctypes.byref(chains.c), int(steps),
                                 _stream(stream)))
 
@@ -401,6 +430,23 @@ def pbn_estimate_two_state(network: Network, soi, omega: int, seed: int, psi0: i
     out = TwoStateReport()
     _check(lib().pbn_estimate_two_state(network.handle, ctypes.byref(q), ctypes.byref(out), _stream(stream)))
     return _as_struct(TwoStateReport, out)
+
+
+def pbn_estimate_two_state_multi(network: Network, sois, omega: int, seed: int, psi0: int = 1024, rhat: float = 1.05,
+                                 eps: float = 1e-10, r: float = 0.005, s: float = 0.95, mode: int = PER_NODE,
+                                 max_length: int = 1 << 26, stream=None) -> dict:
+    """Several properties from the same trajectories (Sec. 4.2, last part);
+    returns the common report with "properties": one dict per property."""
+    props_arg = PropsArg(sois)
+    q = TwoStateQuery(int(omega), int(psi0), float(rhat), float(eps), float(r), float(s), int(max_length), int(seed),
+                      int(mode), SoiArg(None).struct)
+    out = TwoStateReport()
+    each = (PropertyResult * max(1, props_arg.count))()
+    _check(lib().pbn_estimate_two_state_multi(network.handle, ctypes.byref(q), props_arg.count, props_arg.ptr,
+                                              ctypes.byref(out), each, _stream(stream)))
+    rep = _as_struct(TwoStateReport, out)
+    rep["properties"] = [_as_struct(PropertyResult, each[m]) for m in range(props_arg.count)]
+    return rep
 
 
 def pbn_estimate_skart(network: Network, soi, omega: int, seed: int, H_star: float, relative: bool = True,

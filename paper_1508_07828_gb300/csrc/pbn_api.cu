@@ -182,14 +182,42 @@ pbn::SimArgs make_args(const pbn::NetDev &net, const pbn_run_cfg &cfg, const pbn
     static const int stall = getenv("PBN_TEST_STALL_FIRST_TILE") ? atoi(getenv("PBN_TEST_STALL_FIRST_TILE")) : 0;
     a.test_stall = stall;
   }
-  a.soi_size = (ch.bits && ch.bits_cap > 0) ? cfg.soi.size : 0;
+  // state-of-interest entries of every recorded property, flattened
+  const bool bits = ch.bits && ch.bits_cap > 0;
+  const int np = cfg.n_props > 0 ? cfg.n_props : (cfg.soi.size > 0 ? 1 : 0);
   a.soi_val = 0;
-  for (int m = 0; m < cfg.soi.size && m < PBN_MAX_SOI; m++) {
-    a.soi_node[m] = (uint16_t)cfg.soi.nodes[m];
-    if (cfg.soi.values[m]) a.soi_val |= 1u << m;
+  a.soi_size = 0;
+  a.n_props = bits ? np : 0;
+  a.prop_stride = (int64_t)a.G * ch.bits_cap;
+  for (int m = 0; m < np && bits; m++) {
+    const pbn_soi &p = cfg.n_props > 0 ? cfg.props[m] : cfg.soi;
+    for (int e = 0; e < p.size && a.soi_size < PBN_MAX_SOI; e++, a.soi_size++) {
+      a.soi_node[a.soi_size] = (uint16_t)p.nodes[e];
+      a.soi_prop[a.soi_size] = (uint8_t)m;
+      if (p.values[e]) a.soi_val |= 1u << a.soi_size;
+    }
   }
   return a;
 }
+
+// Properties of a run configuration (pbn_run_cfg.n_props / props, else soi).
+int check_props(const pbn_run_cfg &cfg, int n) {
+  if (cfg.n_props < 0 || cfg.n_props > PBN_MAX_PROPERTIES)
+    return fail(PBN_ERR_INVALID, "n_props %d (0 .. %d)", cfg.n_props, PBN_MAX_PROPERTIES);
+  if (cfg.n_props == 0) return check_soi(cfg.soi, n, true);
+  if (!cfg.props) return fail(PBN_ERR_INVALID, "props is NULL");
+  int total = 0;
+  for (int m = 0; m < cfg.n_props; m++) {
+    int rc = check_soi(cfg.props[m], n, false);
+    if (rc) return rc;
+    total += cfg.props[m].size;
+  }
+  if (total > PBN_MAX_SOI) return fail(PBN_ERR_INVALID, "%d state-of-interest entries over all properties (at most %d)",
+                                       total, PBN_MAX_SOI);
+  return PBN_OK;
+}
+
+int n_recorded_props(const pbn_run_cfg &cfg) { return cfg.n_props > 0 ? cfg.n_props : (cfg.soi.size > 0 ? 1 : 0); }
 
 // Select-ahead scratch per (device, stream): the category words of one chunk
 // and, for global perturbation, their per-group OR.  Grown on the stream, so
@@ -233,7 +261,7 @@ struct SelectPlan {
 // shared memory does not fit (staging_req: public values 0, 1, 3; 2 = tiles
 // is not supported).
 int plan_select(const pbn::NetDev &net, int64_t omega, int gpb_req, int threads_req, int T_req, int staging_req,
-                SelectPlan *p) {
+                int n_props, SelectPlan *p) {
   const int G = (int)((omega + 31) / 32);
   const int maxs = pbn::sim_max_smem();
   if (staging_req == 2) return fail(PBN_ERR_UNSUPPORTED, "select-ahead schedule with TMA tiles");
@@ -249,7 +277,7 @@ int plan_select(const pbn::NetDev &net, int64_t omega, int gpb_req, int threads_
       const int st = o[1];
       if (staging_req == 1 && st != pbn::STAGE_SMEM) continue;
       if (staging_req == 3 && st != pbn::STAGE_GLOBAL) continue;
-      const size_t b = pbn::apply_smem_bytes(net.n, net.F, gpb, W, st, o[0]);
+      const size_t b = pbn::apply_smem_bytes(net.n, net.F, gpb, W, st, o[0], n_props);
       if ((int64_t)b <= maxs) {
         p->staging = st;
         p->ring = o[0];
@@ -350,7 +378,7 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
               int64_t *launches = nullptr, ApplyTiming *timing = nullptr) {
   if (steps < 0) return fail(PBN_ERR_INVALID, "negative step count");
   if (steps == 0) return PBN_OK;
-  const bool record = ch.bits && ch.bits_cap > 0 && cfg.soi.size > 0;
+  const bool record = ch.bits && ch.bits_cap > 0 && n_recorded_props(cfg) > 0;
   if (record) {
     const int64_t last = ch.length + steps - 1 - ch.bits_base;
     if (last >= ch.bits_cap) return fail(PBN_ERR_INVALID, "bitstream capacity %lld too small for position %lld",
@@ -373,7 +401,7 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
     SelectPlan sp;
     const std::string saved = g_err;
     int rc = plan_select(net, ch.omega, cfg.groups_per_block, cfg.threads_per_block, cfg.threads_per_item,
-                         cfg.staging, &sp);
+                         cfg.staging, n_recorded_props(cfg), &sp);
     if (rc == PBN_OK) return run_select_ahead(net, cfg, ch, steps, record, sp, s, launches, timing);
     if (cfg.schedule == PBN_SCHEDULE_SELECT_AHEAD) return rc;
     g_err = saved;  // automatic choice: fall back to the fused schedule
@@ -584,7 +612,7 @@ int pbn_run_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *ch, i
   if (ch->omega < 1 || !ch->state) return fail(PBN_ERR_INVALID, "chains not initialised");
   if (cfg->perturb_mode != PBN_PERTURB_PER_NODE && cfg->perturb_mode != PBN_PERTURB_GLOBAL)
     return fail(PBN_ERR_INVALID, "perturb_mode %d", cfg->perturb_mode);
-  int rc = check_soi(cfg->soi, net->dev.n, true);
+  int rc = check_props(*cfg, net->dev.n);
   if (rc) return rc;
   return run_steps(net->dev, *cfg, *ch, steps, (cudaStream_t)stream);
 }
@@ -640,6 +668,11 @@ int pbn_skart(const pbn_chains *ch, int64_t start, int64_t kappa, int64_t bpc, i
 
 namespace {
 
+// Device result slot of a driver query: one statistics result per property,
+// then the device status word, read back with one copy each.
+constexpr size_t kResultBytes = 4096;
+constexpr size_t kStatusOffset = kResultBytes - 64;
+
 // Per-(device, stream) driver workspace, kept across queries so that a query
 // makes no allocation once the buffers have grown to its size: statistics
 // scratch, a device result slot with its pinned host copy, chain state, two
@@ -661,8 +694,8 @@ struct Workspace {
   int setup(cudaStream_t s) {
     if (ready) return PBN_OK;
     CUDA_TRY(pbn::scratch_init(sc, s), "scratch");
-    CUDA_TRY(cudaMalloc(&d_res, 256), "result alloc");
-    CUDA_TRY(cudaMallocHost(&h_res, 256), "pinned alloc");
+    CUDA_TRY(cudaMalloc(&d_res, kResultBytes), "result alloc");
+    CUDA_TRY(cudaMallocHost(&h_res, kResultBytes), "pinned alloc");
     ready = true;
     return PBN_OK;
   }
@@ -744,6 +777,7 @@ struct Query {
   // columns into the other buffer.
   int reserve(int64_t base, int64_t upto) {
     const int G = (int)((ch.omega + 31) / 32);
+    const int rows = G * std::max(1, n_recorded_props(cfg));  // one bitstream per property, one after the other
     if (ch.bits && base >= ch.bits_base && upto - ch.bits_base <= ch.bits_cap) return PBN_OK;
     const int64_t keep_from = std::max(base, ch.bits_base);
     const int64_t kept =
@@ -753,12 +787,12 @@ struct Query {
     cap = (cap + 3) & ~int64_t(3);
     int target = ws.cur_bits;
     if (ch.bits && kept > 0) target ^= 1;   // copy source stays intact
-    int rc = ws.ensure(ws.bits[target], ws.bits_words[target], (size_t)G * cap, s, "bitstream alloc");
+    int rc = ws.ensure(ws.bits[target], ws.bits_words[target], (size_t)rows * cap, s, "bitstream alloc");
     if (rc) return rc;
     uint32_t *nb = ws.bits[target];
     if (ch.bits && kept > 0) {
       CUDA_TRY(cudaMemcpy2DAsync(nb + (keep_from - base), cap * 4, ch.bits + (keep_from - ch.bits_base),
-                                 ch.bits_cap * 4, kept * 4, G, cudaMemcpyDeviceToDevice, s),
+                                 ch.bits_cap * 4, kept * 4, rows, cudaMemcpyDeviceToDevice, s),
                "bitstream copy");
     }
     ws.cur_bits = target;
@@ -799,17 +833,18 @@ struct Query {
   // status word (one synchronisation): a bounded wait that gave up during
   // the query fails it here.
   template <typename T>
-  int fetch(T *h) {
-    static_assert(sizeof(T) <= 192, "result slot");
+  int fetch(T *h, int count = 1) {
+    static_assert(sizeof(T) * PBN_MAX_PROPERTIES <= kStatusOffset, "result slot");
     int *status = pbn::device_status();
     if (!status) return fail(PBN_ERR_CUDA, "device status word unavailable");
-    CUDA_TRY(cudaMemcpyAsync(ws.h_res, d_res, sizeof(T), cudaMemcpyDeviceToHost, s), "result copy");
-    CUDA_TRY(cudaMemcpyAsync((char *)ws.h_res + 192, status, sizeof(int), cudaMemcpyDeviceToHost, s), "status copy");
+    CUDA_TRY(cudaMemcpyAsync(ws.h_res, d_res, sizeof(T) * count, cudaMemcpyDeviceToHost, s), "result copy");
+    CUDA_TRY(cudaMemcpyAsync((char *)ws.h_res + kStatusOffset, status, sizeof(int), cudaMemcpyDeviceToHost, s),
+             "status copy");
     CUDA_TRY(cudaStreamSynchronize(s), "stream sync");
-    memcpy(h, ws.h_res, sizeof(T));
-    d2h_bytes += sizeof(T) + sizeof(int);
+    memcpy(h, ws.h_res, sizeof(T) * count);
+    d2h_bytes += sizeof(T) * count + sizeof(int);
     int st = 0;
-    memcpy(&st, (char *)ws.h_res + 192, sizeof st);
+    memcpy(&st, (char *)ws.h_res + kStatusOffset, sizeof st);
     if (st) {
       CUDA_TRY(cudaMemset(status, 0, sizeof st), "status clear");
       return fail(st, "a bounded device wait gave up during the query");
@@ -817,20 +852,40 @@ struct Query {
     return PBN_OK;
   }
 
-  int gelman_rubin(int64_t psi0, double thr, int64_t max_length, int64_t *psi_out, double *rhat, int32_t *rounds) {
+  // Property m's bitstream as a chain set of its own.
+  pbn_chains view(int m) const {
+    pbn_chains v = ch;
+    v.bits = ch.bits + (size_t)m * ((ch.omega + 31) / 32) * ch.bits_cap;
+    return v;
+  }
+
+  // Alg. GR; with several properties psi doubles until every property's
+  // R-hat is below the threshold (*rhat: the largest, rhat_each[m]: each).
+  int gelman_rubin(int64_t psi0, double thr, int64_t max_length, int64_t *psi_out, double *rhat, int32_t *rounds,
+                   double *rhat_each = nullptr) {
+    const int q = std::max(1, n_recorded_props(cfg));
     int64_t psi = psi0;
     *rounds = 0;
     for (;;) {
       if (2 * psi > max_length) return fail(PBN_ERR_NOT_CONVERGED, "Gelman-Rubin not converged below length %lld", (long long)max_length);
       int rc = extend_to(2 * psi, psi);
       if (rc) return rc;
-      CUDA_TRY(pbn::launch_gelman_rubin(ch, psi - ch.bits_base, psi, (pbn_gr_result *)d_res, sc, s), "G&R");
-      stat_launched(1);
-      pbn_gr_result r;
-      if ((rc = fetch(&r))) return rc;
+      for (int m = 0; m < q; m++)
+        CUDA_TRY(pbn::launch_gelman_rubin(view(m), psi - ch.bits_base, psi, (pbn_gr_result *)d_res + m, sc, s),
+                 "G&R");
+      stat_launched(q);
+      pbn_gr_result r[PBN_MAX_PROPERTIES];
+      if ((rc = fetch(r, q))) return rc;
       (*rounds)++;
-      *rhat = r.rhat;
-      if (r.rhat < thr) { *psi_out = psi; return PBN_OK; }
+      bool all = true;
+      double worst = -INFINITY;
+      for (int m = 0; m < q; m++) {
+        if (rhat_each) rhat_each[m] = r[m].rhat;
+        if (!(r[m].rhat < thr)) all = false;
+        if (!(r[m].rhat <= worst)) worst = r[m].rhat;
+      }
+      *rhat = worst;
+      if (all) { *psi_out = psi; return PBN_OK; }
       psi *= 2;
     }
   }
@@ -884,24 +939,45 @@ int check_query_common(const pbn_net *net, int64_t omega, int64_t psi0, double t
 
 }  // namespace
 
-extern "C" int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_query *q, pbn_two_state_report *out,
-                                      void *stream) {
+namespace {
+
+// Alg. GR then Alg. 3 for one property, or for several properties from the
+// same trajectories (Sec. 4.2, last part): psi doubles until every
+// property's R-hat is below the threshold; every round counts every
+// property; the chains grow by the smallest deficit among the properties
+// whose N exceeds the merged sample until none does; the burn-in check takes
+// the largest M.  With one property every step is Alg. 3's.  `out` carries
+// the common fields and property 0's estimate; each[m] (if given) every
+// property's.
+int two_state_driver(const pbn_net *net, const pbn_two_state_query *q, int n_props, const pbn_soi *props,
+                     pbn_two_state_report *out, pbn_property_result *each, void *stream) {
   if (!q || !out) return fail(PBN_ERR_INVALID, "NULL argument");
-  int rc = check_query_common(net, q->omega, q->psi0, q->rhat_threshold, q->max_length, q->perturb_mode, q->soi);
+  int rc = check_query_common(net, q->omega, q->psi0, q->rhat_threshold, q->max_length, q->perturb_mode,
+                              n_props > 0 ? props[0] : q->soi);
   if (rc) return rc;
   if (!(q->eps > 0 && q->r > 0 && q->s > 0 && q->s < 1)) return fail(PBN_ERR_INVALID, "eps, r, s out of range");
   memset(out, 0, sizeof *out);
   Query Q(net->dev, (cudaStream_t)stream);
   Q.cfg.seed = q->seed;
   Q.cfg.perturb_mode = q->perturb_mode;
-  Q.cfg.soi = q->soi;
+  if (n_props > 0) {
+    Q.cfg.n_props = n_props;
+    Q.cfg.props = props;
+  } else {
+    Q.cfg.soi = q->soi;
+  }
+  if ((rc = check_props(Q.cfg, net->dev.n))) return rc;
+  const int np = std::max(1, n_props);
   if ((rc = Q.open(q->omega))) return rc;
   int64_t psi;
-  if ((rc = Q.gelman_rubin(q->psi0, q->rhat_threshold, q->max_length, &psi, &out->rhat, &out->gr_rounds))) return rc;
+  double rhat_each[PBN_MAX_PROPERTIES];
+  if ((rc = Q.gelman_rubin(q->psi0, q->rhat_threshold, q->max_length, &psi, &out->rhat, &out->gr_rounds,
+                           rhat_each)))
+    return rc;
   out->gr_psi = psi;
   const int64_t omega = q->omega;
-  pbn_two_state_result r;
-  memset(&r, 0, sizeof r);
+  pbn_two_state_result r[PBN_MAX_PROPERTIES];
+  memset(r, 0, sizeof r);
   for (;;) {      // burn-in check (Alg. 3: M against psi)
     for (;;) {    // sample-size check (Alg. 3: N against the merged sample)
       int64_t n = Q.ch.length - psi;
@@ -910,34 +986,56 @@ extern "C" int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_qu
         if ((rc = Q.extend_to(psi + 2, psi))) return rc;
         continue;
       }
-      CUDA_TRY(pbn::launch_two_state(Q.ch, psi - Q.ch.bits_base, n, q->eps, q->r, q->s,
-                                     (pbn_two_state_result *)Q.d_res, Q.sc, Q.s),
-               "two-state");
-      Q.stat_launched(1);
-      if ((rc = Q.fetch(&r))) return rc;
+      for (int m = 0; m < np; m++)
+        CUDA_TRY(pbn::launch_two_state(Q.view(m), psi - Q.ch.bits_base, n, q->eps, q->r, q->s,
+                                       (pbn_two_state_result *)Q.d_res + m, Q.sc, Q.s),
+                 "two-state");
+      Q.stat_launched(np);
+      pbn_two_state_result got[PBN_MAX_PROPERTIES];
+      if ((rc = Q.fetch(got, np))) return rc;
       out->ts_rounds++;
-      if (r.status == PBN_ERR_INSUFFICIENT) {
+      bool insufficient = false;
+      for (int m = 0; m < np; m++) insufficient |= got[m].status == PBN_ERR_INSUFFICIENT;
+      if (insufficient) {
         if (Q.ch.length + n > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "two-state: no transitions below the length cap");
         if ((rc = Q.extend_to(Q.ch.length + n, psi))) return rc;
         continue;
       }
-      if (r.status != PBN_OK) return fail(r.status, "two-state chain is periodic (alpha = beta = 1)");
-      const int64_t deficit = r.N - omega * n;
-      if (deficit <= 0) break;
-      const int64_t extend_by = (deficit + omega - 1) / omega;
+      int64_t smallest = -1;
+      for (int m = 0; m < np; m++) {
+        if (got[m].status != PBN_OK) return fail(got[m].status, "two-state chain is periodic (alpha = beta = 1)");
+        r[m] = got[m];
+        const int64_t deficit = r[m].N - omega * n;
+        if (deficit > 0 && (smallest < 0 || deficit < smallest)) smallest = deficit;
+      }
+      if (smallest < 0) break;
+      const int64_t extend_by = (smallest + omega - 1) / omega;
       if (Q.ch.length + extend_by > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "two-state: length cap");
       if ((rc = Q.extend_to(Q.ch.length + extend_by, psi))) return rc;
     }
-    if (r.M > psi) { psi = r.M; continue; }
+    int64_t Mmax = r[0].M;
+    for (int m = 1; m < np; m++) Mmax = std::max(Mmax, r[m].M);
+    if (Mmax > psi) { psi = Mmax; continue; }
     break;
   }
-  out->prob = r.prob;
-  out->alpha = r.alpha;
-  out->beta = r.beta;
-  out->M = r.M;
-  out->N = r.N;
-  out->ones = r.ones;
-  out->n4[0] = r.n00; out->n4[1] = r.n01; out->n4[2] = r.n10; out->n4[3] = r.n11;
+  out->prob = r[0].prob;
+  out->alpha = r[0].alpha;
+  out->beta = r[0].beta;
+  out->M = r[0].M;
+  out->N = r[0].N;
+  out->ones = r[0].ones;
+  out->n4[0] = r[0].n00; out->n4[1] = r[0].n01; out->n4[2] = r[0].n10; out->n4[3] = r[0].n11;
+  for (int m = 0; each && m < np; m++) {
+    pbn_property_result &e = each[m];
+    e.prob = r[m].prob;
+    e.alpha = r[m].alpha;
+    e.beta = r[m].beta;
+    e.rhat = rhat_each[m];
+    e.M = r[m].M;
+    e.N = r[m].N;
+    e.ones = r[m].ones;
+    e.n4[0] = r[m].n00; e.n4[1] = r[m].n01; e.n4[2] = r[m].n10; e.n4[3] = r[m].n11;
+  }
   {
     int st = 0;
     if ((rc = take_status(&st))) return rc;
@@ -956,6 +1054,21 @@ extern "C" int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_qu
   out->sim_items = Q.sim_items;
   out->d2h_bytes = Q.d2h_bytes;
   return PBN_OK;
+}
+
+}  // namespace
+
+extern "C" int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_query *q, pbn_two_state_report *out,
+                                      void *stream) {
+  return two_state_driver(net, q, 0, nullptr, out, nullptr, stream);
+}
+
+extern "C" int pbn_estimate_two_state_multi(const pbn_net *net, const pbn_two_state_query *q, int32_t n_props,
+                                            const pbn_soi *props, pbn_two_state_report *out,
+                                            pbn_property_result *each, void *stream) {
+  if (n_props < 1 || n_props > PBN_MAX_PROPERTIES || !props)
+    return fail(PBN_ERR_INVALID, "n_props %d (1 .. %d) or props NULL", n_props, PBN_MAX_PROPERTIES);
+  return two_state_driver(net, q, n_props, props, out, each, stream);
 }
 
 extern "C" int pbn_estimate_skart(const pbn_net *net, const pbn_skart_query *q, pbn_skart_report *out, void *stream) {

@@ -818,6 +818,8 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       a.tile_bytes = d.tile_bytes;
       a.status = e->status;
       a.soi_size = (int)q.soi_nodes.size();
+      a.n_props = 1;  // one property per engine query (soi_prop all 0)
+      a.prop_stride = 0;
       for (size_t m = 0; m < q.soi_nodes.size(); m++) {
         a.soi_node[m] = (uint16_t)q.soi_nodes[m];
         if (q.soi_vals[m]) a.soi_val |= 1u << m;

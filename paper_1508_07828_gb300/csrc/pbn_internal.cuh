@@ -10,6 +10,7 @@ namespace pbn {
 
 constexpr int kMaxL = PBN_MAX_FUNCTIONS_PER_NODE;  // functions per node (thresholds per node incl. P32)
 constexpr int kMaxSoi = PBN_MAX_SOI;
+constexpr int kMaxProps = PBN_MAX_PROPERTIES;
 
 // Device tables of one network (built by pbn_load).
 //  node record (processing order r):  bits 0-11 node id, 12-15 l-1, 16-31 first function
@@ -103,6 +104,9 @@ struct SimArgs {
   int W;                 // select-ahead: category words per (step, group), F rounded up to 4
   uint32_t *planes;      // select-ahead: category words [steps][G][W] of the chunk
   uint32_t *anyw;        // select-ahead, global perturbation: [steps][G] OR of the perturbed lanes
+  int n_props;           // properties recorded (entries soi_node[m] belong to property soi_prop[m])
+  int64_t prop_stride;   // words between two properties' bitstreams (G * bits_cap)
+  uint8_t soi_prop[kMaxSoi];
 };
 static_assert(sizeof(SimArgs) % 4 == 0, "SimArgs is copied word by word");
 
@@ -120,7 +124,7 @@ size_t sim_smem_bytes(int n, int F, int gpb, int mode, int staging, int tile_byt
 cudaError_t launch_select(const SimArgs &a, int mode, int BPR, cudaStream_t s);
 // T = threads per (node, group) item: 1, 2 or 4 (each a share of the depth-5 tree).
 cudaError_t launch_apply(const SimArgs &a, int mode, int ring, int T, int threads, size_t smem, cudaStream_t s);
-size_t apply_smem_bytes(int n, int F, int gpb, int W, int staging, int ring);
+size_t apply_smem_bytes(int n, int F, int gpb, int W, int staging, int ring, int n_props);
 int apply_threads_limit(int T);  // largest CTA of the apply variant for T
 // Device status word of the simulation kernels on the current device (0 = ok).
 int *device_status();

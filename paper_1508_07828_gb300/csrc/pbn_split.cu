@@ -24,6 +24,8 @@
 //
 // Both kernels compare the same digits against the same bounds as the fused
 // kernel (draw_below), so the chains are bit-identical under either schedule.
+#include <algorithm>
+
 #include "pbn_step.cuh"
 
 namespace pbn {
@@ -115,13 +117,13 @@ constexpr int kIndRing = 64;
 
 // Ring slots of category words: RING - 1 steps are in flight ahead of the
 // step being applied (8, or 3 when 8 slots do not fit shared memory).
-size_t apply_smem_bytes(int n, int F, int gpb, int W, int staging, int ring) {
+size_t apply_smem_bytes(int n, int F, int gpb, int W, int staging, int ring, int n_props) {
   size_t b = (size_t)ring * gpb * W * 4;                      // category words ring
   b += (size_t)ring * (((size_t)gpb + 3) & ~(size_t)3) * 4;   // OR-of-perturbations ring
   if (staging == STAGE_SMEM) b += (size_t)F * 16;
   b += ((size_t)n * 4 + 15) & ~(size_t)15;                 // node records
   b += 2 * (size_t)n * gpb * 4;                            // current and next state
-  b += (size_t)gpb * kIndRing * 4;                         // indicator words of recent steps
+  b += (size_t)std::max(n_props, 1) * gpb * kIndRing * 4;  // indicator words of recent steps
   return b;
 }
 
@@ -252,12 +254,12 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
   const int items = n * gpb;
   uint32_t *cur = reinterpret_cast<uint32_t *>(p);
   uint32_t *nxt = cur + items;
-  uint32_t *ind = nxt + items;  // [gpb][kIndRing]
+  uint32_t *ind = nxt + items;  // [n_props][gpb][kIndRing]
   for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
     const int i = idx / gpb, gl = idx - i * gpb;
     cur[idx] = gl < ngl ? a.state[(size_t)(g0 + gl) * n + i] : 0u;
   }
-  for (int j = threadIdx.x; j < gpb * kIndRing; j += blockDim.x) ind[j] = kFull;
+  for (int j = threadIdx.x; j < max(a.n_props, 1) * gpb * kIndRing; j += blockDim.x) ind[j] = kFull;
   __syncthreads();  // tables and state staged before any thread reads another's records
   // step s's words of this CTA's groups: one contiguous run of ngl * W words
   const int chunks16 = ngl * W / 4;
@@ -277,7 +279,8 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
   // parameter bank would serialise every step)
   const int my_soi = lane < a.soi_size ? (int)a.soi_node[lane] : 0;
   const bool my_val = (a.soi_val >> lane) & 1u;
-  // indicator of the state of interest after step s (state in `st`)
+  const int my_prop = lane < a.soi_size ? (int)a.soi_prop[lane] : -1;
+  // indicators of the properties after step s (state in `st`)
   auto indicator = [&](const uint32_t *st, int s) {
     if (a.soi_size == 0) return;
     const int64_t col = a.col0 + s;
@@ -287,8 +290,11 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
         const uint32_t w = st[my_soi * gpb + gl];
         v = my_val ? w : ~w;
       }
-      v = __reduce_and_sync(kFull, v);
-      if (lane == 0 && col >= 0) a.bits[(size_t)(g0 + gl) * a.bits_cap + col] = v & lane_mask(a.omega, g0 + gl);
+      for (int m = 0; m < a.n_props; m++) {
+        const uint32_t vm = __reduce_and_sync(kFull, my_prop == m ? v : kFull);
+        if (lane == 0 && col >= 0)
+          a.bits[m * a.prop_stride + (int64_t)(g0 + gl) * a.bits_cap + col] = vm & lane_mask(a.omega, g0 + gl);
+      }
     }
   };
   // start of step s: its words landed and visible, the state after step s-1
@@ -369,24 +375,32 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
     };
     // this item's part of the state of interest: the node must be 1 (need1)
     // and/or 0 (need0; both when the state of interest names it twice)
-    bool need1 = false, need0 = false;
+    // bit m: property m needs the node at 1 (need1) and/or at 0 (need0; both
+    // when a property names it twice)
+    uint32_t need1 = 0u, need0 = 0u;
     if (active && sub == 0)
-      for (int m = 0; m < a.soi_size; m++)
-        if ((int)a.soi_node[m] == node_id(rec)) ((a.soi_val >> m) & 1u ? need1 : need0) = true;
-    const bool in_soi = need1 || need0;
+      for (int e = 0; e < a.soi_size; e++)
+        if ((int)a.soi_node[e] == node_id(rec)) {
+          const uint32_t bit = 1u << a.soi_prop[e];
+          if ((a.soi_val >> e) & 1u) need1 |= bit;
+          else need0 |= bit;
+        }
+    const uint32_t in_props = need1 | need0;
     // store the indicator words of steps s0 .. s0+cnt-1 (complete) and make
     // their ring words ready for reuse
     auto flush = [&](int s0, int cnt) {
       if (a.soi_size == 0) return;
-      for (int g = 0; g < ngl; g++) {
-        const int st = s0 + lane;
-        if (lane < cnt) {
-          uint32_t *word = ind + g * kIndRing + (st & (kIndRing - 1));
-          const int64_t col = a.col0 + st;
-          if (col >= 0) a.bits[(size_t)(g0 + g) * a.bits_cap + col] = *word & lane_mask(a.omega, g0 + g);
-          *word = kFull;
+      for (int m = 0; m < a.n_props; m++)
+        for (int g = 0; g < ngl; g++) {
+          const int st = s0 + lane;
+          if (lane < cnt) {
+            uint32_t *word = ind + (m * gpb + g) * kIndRing + (st & (kIndRing - 1));
+            const int64_t col = a.col0 + st;
+            if (col >= 0)
+              a.bits[m * a.prop_stride + (int64_t)(g0 + g) * a.bits_cap + col] = *word & lane_mask(a.omega, g0 + g);
+            *word = kFull;
+          }
         }
-      }
     };
     if (producer)
       for (int s = 0; s < kRing - 1; s++) issue_warp(s);
@@ -412,8 +426,11 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
         }
         if (active && sub == 0) {
           const uint32_t v = finish(idx, gl, P, fword, ring_any + ring_slot * gpbA);
-          if (in_soi)
-            atomicAnd(ind + gl * kIndRing + (s & (kIndRing - 1)), (need1 ? v : kFull) & (need0 ? ~v : kFull));
+          for (uint32_t props = in_props; props; props &= props - 1) {
+            const int m = __ffs(props) - 1;
+            const uint32_t term = ((need1 >> m) & 1u ? v : kFull) & ((need0 >> m) & 1u ? ~v : kFull);
+            atomicAnd(ind + (m * gpb + gl) * kIndRing + (s & (kIndRing - 1)), term);
+          }
         }
       }
       ring_slot = ring_slot + 1 == kRing ? 0 : ring_slot + 1;

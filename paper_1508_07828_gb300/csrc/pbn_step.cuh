@@ -349,6 +349,7 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
   // parameter bank would serialise every step)
   const int my_soi = lane < a.soi_size ? (int)a.soi_node[lane] : 0;
   const bool my_val = (a.soi_val >> lane) & 1u;
+  const int my_prop = lane < a.soi_size ? (int)a.soi_prop[lane] : -1;
   const int sub = lane & (T - 1);
   const int slot = threadIdx.x / T;
   const int nslots = blockDim.x / T;
@@ -418,8 +419,12 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
           const uint32_t w = nxt[my_soi * gpb + gl];
           v = my_val ? w : ~w;
         }
-        v = __reduce_and_sync(kFull, v);
-        if (lane == 0 && col >= 0) a.bits[(size_t)(g0 + gl) * a.bits_cap + col] = v & lane_mask(a.omega, g0 + gl);
+        // one AND-reduction per property over the lanes of its entries
+        for (int m = 0; m < a.n_props; m++) {
+          const uint32_t vm = __reduce_and_sync(kFull, my_prop == m ? v : kFull);
+          if (lane == 0 && col >= 0)
+            a.bits[m * a.prop_stride + (int64_t)(g0 + gl) * a.bits_cap + col] = vm & lane_mask(a.omega, g0 + gl);
+        }
       }
     }
     uint32_t *tmp = cur;

@@ -51,7 +51,7 @@ STRUCTS = {
     "Soi": ("pbn_soi", ["size", "nodes", "values"]),
     "Chains": ("pbn_chains", ["omega", "state", "bits", "bits_cap", "bits_base", "length"]),
     "RunCfg": ("pbn_run_cfg", ["seed", "perturb_mode", "soi", "groups_per_block", "threads_per_block",
-                               "threads_per_item", "blocks_per_round", "staging", "schedule"]),
+                               "threads_per_item", "blocks_per_round", "staging", "schedule", "n_props", "props"]),
     "GrResult": ("pbn_gr_result", ["rhat", "W", "B", "sigma2", "S1", "S2_lo", "S2_hi"]),
     "TwoStateResult": ("pbn_two_state_result", ["n00", "n01", "n10", "n11", "ones", "alpha", "beta", "prob", "M",
                                                 "N", "status"]),
@@ -64,6 +64,7 @@ STRUCTS = {
                                                 "chain_node_updates", "device_ms", "sim_ms", "sim_launches",
                                                 "kernel_launches", "sim_items", "d2h_bytes", "apply_ms",
                                                 "apply_launches"]),
+    "PropertyResult": ("pbn_property_result", ["prob", "alpha", "beta", "rhat", "M", "N", "ones", "n4"]),
     "SkartQuery": ("pbn_skart_query", ["omega", "psi0", "rhat_threshold", "H_star", "relative", "alpha",
                                        "max_length", "seed", "perturb_mode", "soi"]),
     "SkartReport": ("pbn_skart_report", ["mean", "ci_lo", "ci_hi", "H", "var", "skew", "phi", "rhat", "psi",
