@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="64 networks of uneven size: the engine vs the plain one-query-at-a-time loop")
     ap.add_argument("--serve", action="store_true", help="Poisson arrivals over a pool of 200 networks")
+    ap.add_argument("--multi", type=int, default=0,
+                    help="Q properties from the same trajectories against Q separate queries (mid workload)")
     ap.add_argument("--rates", default="50,200,1000,2000", help="arrival rates (queries/s) for --serve")
     ap.add_argument("--queries", type=int, default=120, help="queries per rate for --serve")
     ap.add_argument("--max-length", type=int, default=1 << 20)
@@ -511,6 +513,55 @@ def run_batched(args):
                       "speedup": pw / bw, "same_updates": pu == bu}))
 
 
+def run_multi(args):
+    """Several properties from the same trajectories (Sec. 4.2, last part) on
+    the mid-size workload: one pbn_estimate_two_state_multi against the loop
+    of one pbn_estimate_two_state per property, same seeds, wall time with
+    the device synchronised on both sides."""
+    import torch
+    import pbn_synth as S
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+    torch.cuda.set_device(0)
+    net, soi, cfg = workload()
+    rng = np.random.default_rng(S.BASE_SEED + 6)
+    props = [soi] + [S.random_soi(rng, net.n, 1, 5) for _ in range(args.multi - 1)]
+    N = P.pbn_load(net)
+    kw = dict(omega=cfg["omega"], psi0=PSI0, rhat=cfg["rhat"], eps=cfg["eps"], r=cfg["r"], s=cfg["s"],
+              max_length=args.max_length)
+
+    def separate(seed):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = [P.pbn_estimate_two_state(N, x, seed=seed, **kw) for x in props]
+        return time.perf_counter() - t0, reps
+
+    def together(seed):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = P.pbn_estimate_two_state_multi(N, props, seed=seed, **kw)
+        return time.perf_counter() - t0, rep
+
+    for k in range(max(1, args.warmup)):
+        separate(k)
+        together(k)
+    ts, tm, upd_s, upd_m = [], [], 0, 0
+    for k in range(args.steps):
+        dt, reps = separate(100 + k)
+        ts.append(dt)
+        upd_s += sum(r["chain_node_updates"] for r in reps)
+        dt, rep = together(100 + k)
+        tm.append(dt)
+        upd_m += rep["chain_node_updates"]
+    print(json.dumps({"mode": "multi", "workload": WORKLOAD, "properties": len(props),
+                      "separate": {"seconds_per_query_set": float(np.median(ts)), "chain_node_updates": upd_s},
+                      "together": {"seconds_per_query_set": float(np.median(tm)), "chain_node_updates": upd_m,
+                                   "length": rep["length"], "psi": rep["psi"]},
+                      "speedup": float(np.median(ts) / np.median(tm)),
+                      "simulation_saved": 1.0 - upd_m / max(upd_s, 1)}))
+
+
 def run_serve(args):
     """Serving: queries arrive as a Poisson process; each names a random
     network of the 200-network pool (n log-uniform in [20, 3000]), a state
@@ -584,6 +635,9 @@ def main():
     args = parse()
     if args.sim_only:
         run_sim_only(args)
+        return
+    if args.multi:
+        run_multi(args)
         return
     if args.batched:
         run_batched(args)
