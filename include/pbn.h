@@ -290,6 +290,38 @@ typedef struct pbn_two_state_report {
 int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_query *q, pbn_two_state_report *out,
                            void *stream);
 
+/* Sequential two-state Markov chain approach on one chain (Sec. 3.1,
+ * Alg. 1): the control of the parallel method (Sec. 5.1 compares the two). */
+typedef struct pbn_two_state_seq_query {
+    int64_t m0, n0;          /* initial burn-in (>= 0) and sample size (>= 2) */
+    double eps, r, s;
+    int64_t max_length;
+    uint64_t seed;           /* chain 0 of this seed's family is simulated */
+    int32_t perturb_mode;
+    pbn_soi soi;
+} pbn_two_state_seq_query;
+
+typedef struct pbn_two_state_seq_report {
+    double prob, alpha, beta;
+    int64_t M, N, length, ones;
+    int64_t n4[4];           /* transitions of the last alpha, beta window */
+    int64_t ab_window;       /* its length */
+    int32_t rounds;
+    int64_t chain_node_updates;   /* length * n */
+    double device_ms, sim_ms;
+    int64_t sim_launches, kernel_launches, d2h_bytes;
+} pbn_two_state_seq_report;
+
+/* Alg. 1: start from length l = m0 + n0; each round extends the chain to
+ * M + N (none in the first), estimates alpha and beta from the last N
+ * positions and recomputes M and N (Alg. 1 line 8), until M + N <= l; the
+ * estimate is the fraction of ones in the last N positions.  A window without
+ * a 0->1 or 1->0 transition doubles N.  Synchronises `stream`.
+ * Errors: PBN_ERR_NOT_CONVERGED (max_length, or alpha = beta = 1),
+ * PBN_ERR_INVALID, PBN_ERR_OOM, PBN_ERR_CUDA. */
+int pbn_estimate_two_state_seq(const pbn_net *net, const pbn_two_state_seq_query *q,
+                               pbn_two_state_seq_report *out, void *stream);
+
 /* One property's part of a multi-property query (Sec. 4.2, last part). */
 typedef struct pbn_property_result {
     double prob, alpha, beta;
@@ -341,6 +373,15 @@ typedef struct pbn_skart_report {
 /* Alg. GR then Alg. 4 (Sec. 4.3) end to end on the device.  Synchronises
  * `stream`.  Errors as pbn_estimate_two_state. */
 int pbn_estimate_skart(const pbn_net *net, const pbn_skart_query *q, pbn_skart_report *out, void *stream);
+
+/* Alg. 2 (Sec. 3.2), the sequential Skart method on chain 0 of the seed's
+ * family (the control of Alg. 4), with Alg. 4's constants: skewness of the
+ * last 1024 of 1280 samples, the randomness test on the whole trajectory with
+ * spacer d, then the CI on the batches after the d skipped ones.  q->omega,
+ * q->psi0 and q->rhat_threshold are ignored; out->psi is the skipped d kappa,
+ * out->batches the batches after it.  Synchronises `stream`.
+ * Errors as pbn_estimate_skart. */
+int pbn_estimate_skart_seq(const pbn_net *net, const pbn_skart_query *q, pbn_skart_report *out, void *stream);
 
 /* ------------------------------------------------- batched / served queries
  *

@@ -19,6 +19,13 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
   norm_ppf, t_ppf    scipy.stats norm.ppf / t.ppf
   skewness           scipy.stats.skew
   estimate_two_state exact answers on small networks (within r)
+  estimate_two_state_seq
+                     Alg. 1 on one chain: the stopping rule, an independent
+                     replay of the final window, exact answers within r,
+                     agreement with the parallel driver within 2r
+  estimate_skart_seq Alg. 2 with the placeholder constants of estimate_skart:
+                     an independent recount of its batch means, coverage on
+                     processes with a known mean; parity unpinned like Alg. 4
   estimate_two_state_multi
                      reduces to estimate_two_state for one property and for
                      repeated copies of it; complementary properties sum to 1
@@ -114,6 +121,8 @@ def lib():
             L.orc_transition_counts.argtypes = [vp, i64, i64, i64, i64, vp]
             L.orc_estimate_two_state.argtypes = [vp, vp, vp, i32, vp]
             L.orc_estimate_two_state_multi.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+            L.orc_estimate_two_state_seq.argtypes = [vp, vp, vp, i32, vp]
+            L.orc_estimate_skart_seq.argtypes = [vp, vp, vp, i32, vp]
             L.orc_skewness.argtypes = [vp, i64]; L.orc_skewness.restype = dbl
             L.orc_vonneumann_pass.argtypes = [vp, i64, i64, i64, dbl, vp]
             L.orc_skart_ci_from_means.argtypes = [vp, i64, i64, dbl, vp]
@@ -267,6 +276,32 @@ def estimate_two_state(net, soi, omega, seed, psi0=1024, rhat=1.05, eps=1e-10, r
     return out
 
 
+class _TwoStateSeqRun(ctypes.Structure):
+    _fields_ = [("m0", ctypes.c_int64), ("n0", ctypes.c_int64), ("max_length", ctypes.c_int64),
+                ("mode", ctypes.c_int32), ("seed", ctypes.c_uint64), ("chain", ctypes.c_int64),
+                ("eps", ctypes.c_double), ("r", ctypes.c_double), ("s", ctypes.c_double),
+                ("prob", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("length", ctypes.c_int64), ("ones", ctypes.c_int64),
+                ("n4", ctypes.c_int64 * 4), ("ab_window", ctypes.c_int64), ("rounds", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
+def estimate_two_state_seq(net, soi, seed, m0=0, n0=1024, eps=1e-10, r=0.005, s=0.95, mode=PER_NODE, chain=0,
+                           max_length=1 << 30) -> dict:
+    """Alg. 1 (sequential two-state Markov chain approach) on chain `chain`
+    of the seed's family."""
+    h = NetHandle(net)
+    nodes, vals = _soi_arrays(soi)
+    run = _TwoStateSeqRun()
+    run.m0, run.n0, run.max_length, run.mode, run.seed, run.chain = m0, n0, max_length, mode, seed, chain
+    run.eps, run.r, run.s = eps, r, s
+    rc = lib().orc_estimate_two_state_seq(h.ref, _ptr(nodes), _ptr(vals), len(nodes), ctypes.byref(run))
+    out = {k: getattr(run, k) for k, _ in _TwoStateSeqRun._fields_ if k != "n4"}
+    out["n4"] = list(run.n4)
+    out["status"] = rc
+    return out
+
+
 class _Property(ctypes.Structure):
     _fields_ = [("prob", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("rhat", ctypes.c_double), ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("ones", ctypes.c_int64),
@@ -310,6 +345,20 @@ def estimate_skart(net, soi, omega, seed, H_star, relative=True, alpha=0.05, psi
     run.omega, run.psi0, run.rhat_threshold, run.max_length = omega, psi0, rhat, max_length
     run.mode, run.seed, run.H_star, run.relative, run.alpha = mode, seed, H_star, int(relative), alpha
     rc = lib().orc_estimate_skart(h.ref, _ptr(nodes), _ptr(vals), len(nodes), ctypes.byref(run))
+    out = {k: getattr(run, k) for k, _ in _SkartRun._fields_}
+    out["status"] = rc
+    return out
+
+
+def estimate_skart_seq(net, soi, seed, H_star, relative=True, alpha=0.05, mode=PER_NODE, max_length=1 << 30) -> dict:
+    """Alg. 2 (sequential Skart) on chain 0 of the seed's family; "psi" is the
+    skipped zeta = d kappa and "batches" the final p'."""
+    h = NetHandle(net)
+    nodes, vals = _soi_arrays(soi)
+    run = _SkartRun()
+    run.omega, run.psi0, run.rhat_threshold, run.max_length = 1, 0, 0.0, max_length
+    run.mode, run.seed, run.H_star, run.relative, run.alpha = mode, seed, H_star, int(relative), alpha
+    rc = lib().orc_estimate_skart_seq(h.ref, _ptr(nodes), _ptr(vals), len(nodes), ctypes.byref(run))
     out = {k: getattr(run, k) for k, _ in _SkartRun._fields_}
     out["status"] = rc
     return out

@@ -384,6 +384,7 @@ typedef struct {
     uint8_t *x;          /* omega * cap indicator history, position j = state j+1 */
     int64_t cap;
     int64_t L;           /* current chain length */
+    int64_t chain0;      /* global index of the first chain (0 unless set) */
 } chains_t;
 
 static int chains_reserve(chains_t *ch, int64_t len) {
@@ -407,8 +408,8 @@ static int chains_extend_to(chains_t *ch, int64_t len) {
     int64_t steps = len - ch->L;
     uint8_t *tmp = (uint8_t *)malloc((size_t)(ch->omega * steps));
     if (!tmp) return ORC_ERR_OOM;
-    rc = orc_simulate(ch->net, ch->mode, ch->seed, ch->omega, (uint64_t)ch->L, steps, ch->states,
-                      ch->soi_nodes, ch->soi_values, ch->soi_size, tmp, steps);
+    rc = orc_simulate_from(ch->net, ch->mode, ch->seed, ch->chain0, ch->omega, (uint64_t)ch->L, steps, ch->states,
+                           ch->soi_nodes, ch->soi_values, ch->soi_size, tmp, steps);
     for (int64_t c = 0; c < ch->omega; c++) memcpy(ch->x + c * ch->cap + ch->L, tmp + c * steps, (size_t)steps);
     free(tmp);
     ch->L = len;
@@ -541,6 +542,87 @@ int orc_estimate_two_state(const orc_net *net, const int32_t *soi_nodes, const u
         run->length = ch.L;
         run->sample_size = omega * n;
         run->prob = (double)ones / (double)(omega * n);
+    }
+done:
+    run->status = rc;
+    chains_close(&ch);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sequential two-state Markov chain approach (Sec. 3.1, Alg. 1).               */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    /* inputs */
+    int64_t m0, n0;          /* initial burn-in and sample size */
+    int64_t max_length;
+    int32_t mode;
+    uint64_t seed;
+    int64_t chain;           /* which chain of the seed's family is simulated */
+    double eps, r, s;
+    /* outputs */
+    double prob, alpha, beta;
+    int64_t M, N, length, ones;
+    int64_t n4[4];           /* transitions of the last alpha, beta window */
+    int64_t ab_window;       /* its length (the N of the round before the last) */
+    int32_t rounds;
+    int32_t status;
+} orc_two_state_seq_run;
+
+/*
+ * Alg. 1 on one chain: start from length l = m0 + n0; in each round extend
+ * the trajectory to M + N (no-op in the first round), l := M + N, estimate
+ * alpha and beta from transitions within the last N positions, recompute M
+ * and N by Alg. 1 line 8; stop when M + N <= l; the estimate is the fraction
+ * of ones in the last N positions.  Read where the text is silent: a window
+ * without a 0->1 or a 1->0 transition (or shorter than 2) cannot give alpha
+ * and beta, so N doubles and the round repeats; alpha = beta = 1 (a periodic
+ * two-state chain) is not converged.
+ */
+int orc_estimate_two_state_seq(const orc_net *net, const int32_t *soi_nodes, const uint8_t *soi_values,
+                               int32_t soi_size, orc_two_state_seq_run *run) {
+    if (run->m0 < 0 || run->n0 < 2) return ORC_ERR_INVALID;
+    chains_t ch;
+    int rc = chains_open(&ch, net, run->mode, run->seed, 1, soi_nodes, soi_values, soi_size);
+    if (rc) return rc;
+    /* chain `chain` of the seed's family: its own initial state and draws */
+    orc_init_states_from(net, run->seed, run->chain, 1, ch.states);
+    ch.chain0 = run->chain;
+    int64_t M = run->m0, N = run->n0, l = M + N;
+    run->rounds = 0;
+    if (l > run->max_length) { rc = ORC_ERR_NOT_CONVERGED; goto done; }
+    if ((rc = chains_extend_to(&ch, l))) goto done;
+    for (;;) {
+        if (M + N > l) {
+            if (M + N > run->max_length) { rc = ORC_ERR_NOT_CONVERGED; goto done; }
+            if ((rc = chains_extend_to(&ch, M + N))) goto done;
+            l = M + N;
+        }
+        run->rounds++;
+        int64_t c[4];
+        const int64_t start = l - N;
+        orc_transition_counts(ch.x, 1, ch.cap, start, N, c);
+        memcpy(run->n4, c, sizeof(c));
+        run->ab_window = N;
+        if (N < 2 || c[1] == 0 || c[2] == 0 || (c[0] + c[1]) == 0 || (c[2] + c[3]) == 0) {
+            N = 2 * (N < 2 ? 2 : N);
+            continue;
+        }
+        double a = (double)c[1] / (double)(c[0] + c[1]);
+        double b = (double)c[2] / (double)(c[2] + c[3]);
+        int64_t M1, N1;
+        if ((rc = orc_two_state_MN(a, b, run->eps, run->r, run->s, &M1, &N1))) goto done;
+        run->alpha = a; run->beta = b;
+        M = M1; N = N1;
+        if (M + N <= l) break;
+    }
+    {
+        int64_t ones = 0;
+        for (int64_t j = l - N; j < l; j++) ones += ch.x[j];
+        run->ones = ones;
+        run->prob = (double)ones / (double)N;
+        run->M = M; run->N = N; run->length = l;
     }
 done:
     run->status = rc;
@@ -986,6 +1068,105 @@ int orc_estimate_skart(const orc_net *net, const int32_t *soi_nodes, const uint8
     run->kappa = kappa;
     run->batches = p;
     run->sample_size = kappa * p;
+done:
+    free(buf);
+    run->status = rc;
+    chains_close(&ch);
+    return rc;
+}
+
+/*
+ * Alg. 2 (Sec. 3.2), the sequential Skart method on chain 0 of the seed's
+ * family, with the constants of this build's Alg. 4 (placeholders for the
+ * Skart reference, see orc_estimate_skart):
+ *  - eta = 1280 samples; skewness of the last 1024 gives the batch size
+ *    (16 when |skewness| > 4, else 1); p := eta batches, eta := kappa p;
+ *  - the randomness test runs on the batch means of the whole trajectory
+ *    with spacer d, adjusting (d, kappa, p) as Alg. 4 does until it passes;
+ *  - then zeta = d kappa samples are skipped and the CI uses the p' = p - d
+ *    nonspaced batches after them; when H > H* the batch size and count are
+ *    adjusted as in Alg. 4 and eta := kappa (p' + d), the skipped part being
+ *    d batches of the current size.
+ * run->psi reports the skipped zeta; run->batches the final p'.
+ */
+int orc_estimate_skart_seq(const orc_net *net, const int32_t *soi_nodes, const uint8_t *soi_values,
+                           int32_t soi_size, orc_skart_run *run) {
+    chains_t ch;
+    int rc = chains_open(&ch, net, run->mode, run->seed, 1, soi_nodes, soi_values, soi_size);
+    if (rc) return rc;
+    double *buf = NULL;
+    run->gr_rounds = 0;
+    run->rhat = 0.0;
+    int64_t eta = 1280;
+    const int64_t l = 1024;
+    if (eta > run->max_length) { rc = ORC_ERR_NOT_CONVERGED; goto done; }
+    if ((rc = chains_extend_to(&ch, eta))) goto done;
+    {
+        buf = (double *)malloc(sizeof(double) * (size_t)l);
+        if (!buf) { rc = ORC_ERR_OOM; goto done; }
+        for (int64_t j = 0; j < l; j++) buf[j] = ch.x[eta - l + j];
+        double B = orc_skewness(buf, l);
+        free(buf); buf = NULL;
+        run->kappa = fabs(B) > 4.0 ? 16 : 1;
+    }
+    int64_t kappa = run->kappa;
+    int64_t p = eta;
+    eta = kappa * p;
+    int64_t d = 0;
+    const double alpha_ran = 0.20;
+    run->rand_rounds = 0;
+    for (;;) {
+        if (eta > run->max_length) { rc = ORC_ERR_NOT_CONVERGED; goto done; }
+        if ((rc = chains_extend_to(&ch, eta))) goto done;
+        buf = (double *)malloc(sizeof(double) * (size_t)p);
+        if (!buf) { rc = ORC_ERR_OOM; goto done; }
+        batch_means(&ch, 0, kappa, p, buf);
+        double C;
+        int pass = orc_vonneumann_pass(buf, 1, p, d, alpha_ran, &C);
+        free(buf); buf = NULL;
+        run->rand_rounds++;
+        if (pass) break;
+        d += 1;
+        if (d > 10) {
+            d = 0;
+            kappa = (int64_t)ceil(sqrt(2.0) * (double)kappa);
+            p = (int64_t)ceil(0.9 * (double)p);
+        }
+        eta = kappa * p;
+    }
+    run->spacer = d;
+    int64_t pp = p - d;           /* batches after the skipped d */
+    if (pp < 2) { rc = ORC_ERR_NOT_CONVERGED; goto done; }
+    run->ci_rounds = 0;
+    for (;;) {
+        eta = kappa * (pp + d);
+        if (eta > run->max_length) { rc = ORC_ERR_NOT_CONVERGED; goto done; }
+        if ((rc = chains_extend_to(&ch, eta))) goto done;
+        buf = (double *)malloc(sizeof(double) * (size_t)pp);
+        if (!buf) { rc = ORC_ERR_OOM; goto done; }
+        batch_means(&ch, d * kappa, kappa, pp, buf);
+        orc_skart_ci ci;
+        orc_skart_ci_from_means(buf, 1, pp, run->alpha, &ci);
+        free(buf); buf = NULL;
+        run->ci_rounds++;
+        run->mean = ci.mean; run->ci_lo = ci.ci_lo; run->ci_hi = ci.ci_hi; run->H = ci.H;
+        run->var = ci.var; run->skew = ci.skew; run->phi = ci.phi;
+        double Hs = run->relative ? run->H_star * fabs(ci.mean) : run->H_star;
+        if (!(ci.H > Hs)) break;
+        double f = (ci.H / Hs) * (ci.H / Hs);
+        int64_t pmax = pp > 1024 ? pp : 1024;
+        double pf = ceil(f * (double)pp);
+        int64_t p1 = pf > (double)pmax ? pmax : (int64_t)pf;
+        int64_t k1 = (int64_t)ceil((double)kappa * f * (double)pp / (double)p1);
+        if (k1 < kappa) k1 = kappa;
+        kappa = k1;
+        pp = p1;
+    }
+    run->psi = d * kappa;
+    run->length = ch.L;
+    run->kappa = kappa;
+    run->batches = pp;
+    run->sample_size = kappa * pp;
 done:
     free(buf);
     run->status = rc;

@@ -100,6 +100,18 @@ class TwoStateReport(ctypes.Structure):
                 ("apply_launches", c_i64)]
 
 
+class TwoStateSeqQuery(ctypes.Structure):
+    _fields_ = [("m0", c_i64), ("n0", c_i64), ("eps", c_dbl), ("r", c_dbl), ("s", c_dbl), ("max_length", c_i64),
+                ("seed", c_u64), ("perturb_mode", c_i32), ("soi", Soi)]
+
+
+class TwoStateSeqReport(ctypes.Structure):
+    _fields_ = [("prob", c_dbl), ("alpha", c_dbl), ("beta", c_dbl), ("M", c_i64), ("N", c_i64), ("length", c_i64),
+                ("ones", c_i64), ("n4", c_i64 * 4), ("ab_window", c_i64), ("rounds", c_i32),
+                ("chain_node_updates", c_i64), ("device_ms", c_dbl), ("sim_ms", c_dbl), ("sim_launches", c_i64),
+                ("kernel_launches", c_i64), ("d2h_bytes", c_i64)]
+
+
 class PropertyResult(ctypes.Structure):
     _fields_ = [("prob", c_dbl), ("alpha", c_dbl), ("beta", c_dbl), ("rhat", c_dbl), ("M", c_i64), ("N", c_i64),
                 ("ones", c_i64), ("n4", c_i64 * 4)]
@@ -170,6 +182,8 @@ def lib():
             L.pbn_estimate_two_state.argtypes = [c_vp, P(TwoStateQuery), P(TwoStateReport), c_vp]
             L.pbn_estimate_two_state_multi.argtypes = [c_vp, P(TwoStateQuery), c_i32, c_vp, P(TwoStateReport),
                                                        P(PropertyResult), c_vp]
+            L.pbn_estimate_two_state_seq.argtypes = [c_vp, P(TwoStateSeqQuery), P(TwoStateSeqReport), c_vp]
+            L.pbn_estimate_skart_seq.argtypes = [c_vp, P(SkartQuery), P(SkartReport), c_vp]
             L.pbn_estimate_skart.argtypes = [c_vp, P(SkartQuery), P(SkartReport), c_vp]
             L.pbn_engine_create.argtypes = [P(EngineCfg), c_vp, P(c_vp)]
             L.pbn_engine_destroy.argtypes = [c_vp]
@@ -432,6 +446,19 @@ def pbn_estimate_two_state(network: Network, soi, omega: int, seed: int, psi0: i
     return _as_struct(TwoStateReport, out)
 
 
+def pbn_estimate_two_state_seq(network: Network, soi, seed: int, m0: int = 0, n0: int = 1024, eps: float = 1e-10,
+                               r: float = 0.005, s: float = 0.95, mode: int = PER_NODE, max_length: int = 1 << 30,
+                               stream=None) -> dict:
+    """Alg. 1 (sequential two-state Markov chain approach) on chain 0 of the
+    seed's family: the control run of the parallel method."""
+    soi_arg = SoiArg(soi)
+    q = TwoStateSeqQuery(int(m0), int(n0), float(eps), float(r), float(s), int(max_length), int(seed), int(mode),
+                         soi_arg.struct)
+    out = TwoStateSeqReport()
+    _check(lib().pbn_estimate_two_state_seq(network.handle, ctypes.byref(q), ctypes.byref(out), _stream(stream)))
+    return _as_struct(TwoStateSeqReport, out)
+
+
 def pbn_estimate_two_state_multi(network: Network, sois, omega: int, seed: int, psi0: int = 1024, rhat: float = 1.05,
                                  eps: float = 1e-10, r: float = 0.005, s: float = 0.95, mode: int = PER_NODE,
                                  max_length: int = 1 << 26, stream=None) -> dict:
@@ -458,6 +485,18 @@ def pbn_estimate_skart(network: Network, soi, omega: int, seed: int, H_star: flo
                    int(max_length), int(seed), int(mode), soi_arg.struct)
     out = SkartReport()
     _check(lib().pbn_estimate_skart(network.handle, ctypes.byref(q), ctypes.byref(out), _stream(stream)))
+    return _as_struct(SkartReport, out)
+
+
+def pbn_estimate_skart_seq(network: Network, soi, seed: int, H_star: float, relative: bool = True,
+                           alpha: float = 0.05, mode: int = PER_NODE, max_length: int = 1 << 30,
+                           stream=None) -> dict:
+    """Alg. 2 (sequential Skart) on chain 0 of the seed's family."""
+    soi_arg = SoiArg(soi)
+    q = SkartQuery(1, 0, 0.0, float(H_star), int(bool(relative)), float(alpha), int(max_length), int(seed),
+                   int(mode), soi_arg.struct)
+    out = SkartReport()
+    _check(lib().pbn_estimate_skart_seq(network.handle, ctypes.byref(q), ctypes.byref(out), _stream(stream)))
     return _as_struct(SkartReport, out)
 
 

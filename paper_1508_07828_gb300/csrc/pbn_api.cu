@@ -1063,12 +1063,187 @@ extern "C" int pbn_estimate_two_state(const pbn_net *net, const pbn_two_state_qu
   return two_state_driver(net, q, 0, nullptr, out, nullptr, stream);
 }
 
+extern "C" int pbn_estimate_two_state_seq(const pbn_net *net, const pbn_two_state_seq_query *q,
+                                          pbn_two_state_seq_report *out, void *stream) {
+  if (!net || !q || !out) return fail(PBN_ERR_INVALID, "NULL argument");
+  if (q->m0 < 0 || q->n0 < 2) return fail(PBN_ERR_INVALID, "m0 %lld (>= 0), n0 %lld (>= 2)", (long long)q->m0,
+                                          (long long)q->n0);
+  if (q->perturb_mode != PBN_PERTURB_PER_NODE && q->perturb_mode != PBN_PERTURB_GLOBAL)
+    return fail(PBN_ERR_INVALID, "perturb_mode %d", q->perturb_mode);
+  if (!(q->eps > 0 && q->r > 0 && q->s > 0 && q->s < 1)) return fail(PBN_ERR_INVALID, "eps, r, s out of range");
+  int rc = check_soi(q->soi, net->dev.n, false);
+  if (rc) return rc;
+  memset(out, 0, sizeof *out);
+  Query Q(net->dev, (cudaStream_t)stream);
+  Q.cfg.seed = q->seed;
+  Q.cfg.perturb_mode = q->perturb_mode;
+  Q.cfg.soi = q->soi;
+  if ((rc = Q.open(1))) return rc;
+  // The whole trajectory stays recorded: the final window (last N) may start
+  // before the last alpha, beta window when N grows while M shrinks.
+  int64_t M = q->m0, N = q->n0, l = M + N;
+  if (l > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "sequential two-state: length cap");
+  if ((rc = Q.extend_to(l, 0))) return rc;
+  pbn_two_state_result r;
+  for (;;) {
+    if (M + N > l) {
+      if (M + N > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "sequential two-state: length cap");
+      if ((rc = Q.extend_to(M + N, 0))) return rc;
+      l = M + N;
+    }
+    out->rounds++;
+    CUDA_TRY(pbn::launch_two_state(Q.ch, l - N - Q.ch.bits_base, N, q->eps, q->r, q->s,
+                                   (pbn_two_state_result *)Q.d_res, Q.sc, Q.s),
+             "two-state");
+    Q.stat_launched(1);
+    if ((rc = Q.fetch(&r))) return rc;
+    out->n4[0] = r.n00; out->n4[1] = r.n01; out->n4[2] = r.n10; out->n4[3] = r.n11;
+    out->ab_window = N;
+    if (r.status == PBN_ERR_INSUFFICIENT) {
+      N = 2 * N;
+      continue;
+    }
+    if (r.status != PBN_OK) return fail(r.status, "two-state chain is periodic (alpha = beta = 1)");
+    out->alpha = r.alpha;
+    out->beta = r.beta;
+    M = r.M;
+    N = r.N;
+    if (M + N <= l) break;
+  }
+  // the estimate over the last N positions (the kernel's ones count; its
+  // two-state status does not matter here)
+  CUDA_TRY(pbn::launch_two_state(Q.ch, l - N - Q.ch.bits_base, N, q->eps, q->r, q->s,
+                                 (pbn_two_state_result *)Q.d_res, Q.sc, Q.s),
+           "two-state");
+  Q.stat_launched(1);
+  if ((rc = Q.fetch(&r))) return rc;
+  {
+    int st = 0;
+    if ((rc = take_status(&st))) return rc;
+    if (st) return fail(st, "a bounded device wait gave up during the query");
+  }
+  out->ones = r.ones;
+  out->prob = (double)r.ones / (double)N;
+  out->M = M;
+  out->N = N;
+  out->length = l;
+  out->chain_node_updates = l * (int64_t)net->dev.n;
+  out->device_ms = Q.elapsed_ms();
+  out->sim_ms = Q.sim_ms();
+  out->sim_launches = Q.sim_launches;
+  out->kernel_launches = Q.kernel_launches;
+  out->d2h_bytes = Q.d2h_bytes;
+  return PBN_OK;
+}
+
 extern "C" int pbn_estimate_two_state_multi(const pbn_net *net, const pbn_two_state_query *q, int32_t n_props,
                                             const pbn_soi *props, pbn_two_state_report *out,
                                             pbn_property_result *each, void *stream) {
   if (n_props < 1 || n_props > PBN_MAX_PROPERTIES || !props)
     return fail(PBN_ERR_INVALID, "n_props %d (1 .. %d) or props NULL", n_props, PBN_MAX_PROPERTIES);
   return two_state_driver(net, q, n_props, props, out, each, stream);
+}
+
+// Alg. 2 (Sec. 3.2) on chain 0 of the seed's family, with the same constants
+// as the parallel driver below (placeholders for the Skart reference):
+// skewness of the last 1024 of 1280 samples; the randomness test on the whole
+// trajectory's batch means with spacer d; then the CI on the p' = p - d
+// nonspaced batches after the skipped d kappa samples, eta := kappa (p' + d).
+extern "C" int pbn_estimate_skart_seq(const pbn_net *net, const pbn_skart_query *q, pbn_skart_report *out,
+                                      void *stream) {
+  if (!net || !q || !out) return fail(PBN_ERR_INVALID, "NULL argument");
+  if (q->perturb_mode != PBN_PERTURB_PER_NODE && q->perturb_mode != PBN_PERTURB_GLOBAL)
+    return fail(PBN_ERR_INVALID, "perturb_mode %d", q->perturb_mode);
+  if (!(q->H_star > 0 && q->alpha > 0 && q->alpha < 1)) return fail(PBN_ERR_INVALID, "H_star, alpha");
+  int rc = check_soi(q->soi, net->dev.n, false);
+  if (rc) return rc;
+  memset(out, 0, sizeof *out);
+  Query Q(net->dev, (cudaStream_t)stream);
+  Q.cfg.seed = q->seed;
+  Q.cfg.perturb_mode = q->perturb_mode;
+  Q.cfg.soi = q->soi;
+  if ((rc = Q.open(1))) return rc;
+  int64_t eta = 1280;
+  const int64_t l = 1024;
+  if (eta > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "sequential Skart: length cap");
+  if ((rc = Q.extend_to(eta, 0))) return rc;
+  pbn_skart_result sk;
+  // skewness of the last l samples: batch size 1, one batch per sample
+  CUDA_TRY(pbn::launch_skart(Q.ch, eta - l - Q.ch.bits_base, 1, l, 0, q->alpha, 0.20, (pbn_skart_result *)Q.d_res,
+                             Q.sc, Q.s),
+           "Skart");
+  Q.stat_launched(2);
+  if ((rc = Q.fetch(&sk))) return rc;
+  int64_t kappa = fabs(sk.skew) > 4.0 ? 16 : 1;
+  int64_t p = eta;
+  eta = kappa * p;
+  int64_t d = 0;
+  const double alpha_ran = 0.20;
+  for (;;) {  // randomness test on the whole trajectory
+    if (eta > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "sequential Skart: length cap");
+    if ((rc = Q.extend_to(eta, 0))) return rc;
+    CUDA_TRY(pbn::launch_skart(Q.ch, 0 - Q.ch.bits_base, kappa, p, d, q->alpha, alpha_ran,
+                               (pbn_skart_result *)Q.d_res, Q.sc, Q.s),
+             "Skart");
+    Q.stat_launched(2);
+    if ((rc = Q.fetch(&sk))) return rc;
+    out->rand_rounds++;
+    if (sk.vn_pass) break;
+    d += 1;
+    if (d > 10) {
+      d = 0;
+      kappa = (int64_t)ceil(sqrt(2.0) * (double)kappa);
+      p = (int64_t)ceil(0.9 * (double)p);
+    }
+    eta = kappa * p;
+  }
+  out->spacer = d;
+  int64_t pp = p - d;  // batches after the d skipped ones
+  if (pp < 2) return fail(PBN_ERR_NOT_CONVERGED, "sequential Skart: fewer than 2 batches after the spacer");
+  for (;;) {  // CI loop
+    eta = kappa * (pp + d);
+    if (eta > q->max_length) return fail(PBN_ERR_NOT_CONVERGED, "sequential Skart: length cap");
+    if (kappa > (1ll << 30)) return fail(PBN_ERR_UNSUPPORTED, "Skart batch size above 2^30");
+    if ((rc = Q.extend_to(eta, 0))) return rc;
+    CUDA_TRY(pbn::launch_skart(Q.ch, d * kappa - Q.ch.bits_base, kappa, pp, 0, q->alpha, alpha_ran,
+                               (pbn_skart_result *)Q.d_res, Q.sc, Q.s),
+             "Skart");
+    Q.stat_launched(2);
+    if ((rc = Q.fetch(&sk))) return rc;
+    out->ci_rounds++;
+    out->mean = sk.mean; out->ci_lo = sk.ci_lo; out->ci_hi = sk.ci_hi; out->H = sk.H;
+    out->var = sk.var; out->skew = sk.skew; out->phi = sk.phi;
+    const double Hs = q->relative ? q->H_star * fabs(sk.mean) : q->H_star;
+    if (!(sk.H > Hs)) break;
+    const double f = (sk.H / Hs) * (sk.H / Hs);
+    const int64_t pmax = pp > 1024 ? pp : 1024;
+    const double pf = ceil(f * (double)pp);
+    const int64_t p1 = pf > (double)pmax ? pmax : (int64_t)pf;
+    int64_t k1 = (int64_t)ceil((double)kappa * f * (double)pp / (double)p1);
+    if (k1 < kappa) k1 = kappa;
+    kappa = k1;
+    pp = p1;
+  }
+  {
+    int st = 0;
+    if ((rc = take_status(&st))) return rc;
+    if (st) return fail(st, "a bounded device wait gave up during the query");
+  }
+  out->psi = d * kappa;
+  out->length = Q.ch.length;
+  out->kappa = kappa;
+  out->batches = pp;
+  out->sample_size = kappa * pp;
+  out->chain_node_updates = Q.ch.length * (int64_t)net->dev.n;
+  out->device_ms = Q.elapsed_ms();
+  out->sim_ms = Q.sim_ms();
+  out->sim_launches = Q.sim_launches;
+  out->apply_ms = Q.apply_ms();
+  out->apply_launches = (int64_t)Q.apply_timing.pairs.size();
+  out->kernel_launches = Q.kernel_launches;
+  out->sim_items = Q.sim_items;
+  out->d2h_bytes = Q.d2h_bytes;
+  return PBN_OK;
 }
 
 extern "C" int pbn_estimate_skart(const pbn_net *net, const pbn_skart_query *q, pbn_skart_report *out, void *stream) {

@@ -64,6 +64,11 @@ STRUCTS = {
                                                 "chain_node_updates", "device_ms", "sim_ms", "sim_launches",
                                                 "kernel_launches", "sim_items", "d2h_bytes", "apply_ms",
                                                 "apply_launches"]),
+    "TwoStateSeqQuery": ("pbn_two_state_seq_query", ["m0", "n0", "eps", "r", "s", "max_length", "seed",
+                                                     "perturb_mode", "soi"]),
+    "TwoStateSeqReport": ("pbn_two_state_seq_report", ["prob", "alpha", "beta", "M", "N", "length", "ones", "n4",
+                                                       "ab_window", "rounds", "chain_node_updates", "device_ms",
+                                                       "sim_ms", "sim_launches", "kernel_launches", "d2h_bytes"]),
     "PropertyResult": ("pbn_property_result", ["prob", "alpha", "beta", "rhat", "M", "N", "ones", "n4"]),
     "SkartQuery": ("pbn_skart_query", ["omega", "psi0", "rhat_threshold", "H_star", "relative", "alpha",
                                        "max_length", "seed", "perturb_mode", "soi"]),
