@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="64 networks of uneven size: the engine vs the plain one-query-at-a-time loop")
     ap.add_argument("--serve", action="store_true", help="Poisson arrivals over a pool of 200 networks")
+    ap.add_argument("--seq", action="store_true",
+                    help="sequential Alg. 1 on one chain against the parallel query (speed-up, speed-up E)")
+    ap.add_argument("--seq-r", type=float, default=1e-4,
+                    help="precision r of the --seq comparison (the paper's experiments use 1e-4)")
     ap.add_argument("--multi", type=int, default=0,
                     help="Q properties from the same trajectories against Q separate queries (mid workload)")
     ap.add_argument("--rates", default="50,200,1000,2000", help="arrival rates (queries/s) for --serve")
@@ -562,6 +566,48 @@ def run_multi(args):
                       "simulation_saved": 1.0 - upd_m / max(upd_s, 1)}))
 
 
+def run_seq(args):
+    """The paper's speed-up (Sec. 5.1) on one GPU: the sequential Alg. 1 on
+    one chain against the parallel Alg. GR + Alg. 3 on the bench workload's
+    chains, same property and precision; E = speed-up x parallel sample size /
+    sequential sample size removes the effect of the sample sizes drawn."""
+    import torch
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+    torch.cuda.set_device(0)
+    net, soi, cfg = workload()
+    N = P.pbn_load(net)
+    r = args.seq_r
+    par_kw = dict(omega=cfg["omega"], psi0=PSI0, rhat=cfg["rhat"], eps=cfg["eps"], r=r, s=cfg["s"],
+                  max_length=args.max_length)
+    seq_kw = dict(m0=0, n0=PSI0, eps=cfg["eps"], r=r, s=cfg["s"])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = fn()
+        return time.perf_counter() - t0, rep
+
+    timed(lambda: P.pbn_estimate_two_state(N, soi, seed=1, **par_kw))
+    timed(lambda: P.pbn_estimate_two_state_seq(N, soi, seed=1, **seq_kw))
+    rows = []
+    for k in range(args.steps):
+        tp, rp = timed(lambda: P.pbn_estimate_two_state(N, soi, seed=100 + k, **par_kw))
+        ts, rs = timed(lambda: P.pbn_estimate_two_state_seq(N, soi, seed=200 + k, **seq_kw))
+        sp = ts / tp
+        rows.append({"t_par_s": tp, "t_seq_s": ts, "size_par": rp["sample_size"], "size_seq": rs["N"],
+                     "len_seq": rs["length"], "prob_par": rp["prob"], "prob_seq": rs["prob"], "speedup": sp,
+                     "speedup_E": sp * rp["sample_size"] / rs["N"]})
+    med = lambda key: float(np.median([r[key] for r in rows]))
+    agree = float(np.mean([abs(x["prob_par"] - x["prob_seq"]) < 2 * r for x in rows]))
+    print(json.dumps({"mode": "seq-vs-par", "workload": WORKLOAD.replace("r0.005", f"r{r:g}"), "runs": len(rows),
+                      "chains": cfg["omega"], "r": r,
+                      "t_par_s": med("t_par_s"), "t_seq_s": med("t_seq_s"), "speedup": med("speedup"),
+                      "speedup_E": med("speedup_E"), "size_par": med("size_par"), "size_seq": med("size_seq"),
+                      "seq_length": med("len_seq"), "agreement_within_2r": agree}))
+
+
 def run_serve(args):
     """Serving: queries arrive as a Poisson process; each names a random
     network of the 200-network pool (n log-uniform in [20, 3000]), a state
@@ -638,6 +684,9 @@ def main():
         return
     if args.multi:
         run_multi(args)
+        return
+    if args.seq:
+        run_seq(args)
         return
     if args.batched:
         run_batched(args)
