@@ -66,7 +66,7 @@ def build(force: bool = False) -> str:
 class _Net(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("F", ctypes.c_int32),
                 ("fn_offset", ctypes.c_void_p), ("par_offset", ctypes.c_void_p),
-                ("parents", ctypes.c_void_p), ("truth_table", ctypes.c_void_p),
+                ("parents", ctypes.c_void_p), ("tt_offset", ctypes.c_void_p), ("tt_words", ctypes.c_void_p),
                 ("select_prob", ctypes.c_void_p), ("p", ctypes.c_double)]
 
 
@@ -142,11 +142,13 @@ class NetHandle:
         self.fn_offset = np.ascontiguousarray(net.fn_offset, dtype=np.int32)
         self.par_offset = np.ascontiguousarray(net.par_offset, dtype=np.int32)
         self.parents = np.ascontiguousarray(net.parents if len(net.parents) else np.zeros(1, np.int32), dtype=np.int32)
-        self.truth_table = np.ascontiguousarray(net.truth_table, dtype=np.uint32)
+        self.tt_offset = np.ascontiguousarray(net.tt_offset, dtype=np.int32)
+        self.tt_words = np.ascontiguousarray(net.tt_words, dtype=np.uint32)
         self.select_prob = np.ascontiguousarray(net.select_prob, dtype=np.float64)
         self.n = int(net.n)
         self.s = _Net(self.n, int(self.fn_offset[-1]), self.fn_offset.ctypes.data, self.par_offset.ctypes.data,
-                      self.parents.ctypes.data, self.truth_table.ctypes.data, self.select_prob.ctypes.data,
+                      self.parents.ctypes.data, self.tt_offset.ctypes.data, self.tt_words.ctypes.data,
+                      self.select_prob.ctypes.data,
                       float(net.p))
 
     @property

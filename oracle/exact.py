@@ -65,7 +65,8 @@ def function_values(net, states: np.ndarray) -> np.ndarray:
         idx = np.zeros(S, dtype=np.int64)
         for m, v in enumerate(par):
             idx |= ((states >> int(v)) & 1) << m
-        vals[:, f] = (int(net.truth_table[f]) >> idx) & 1
+        words = np.asarray(net.tt_of(f), dtype=np.int64)
+        vals[:, f] = (words[idx >> 5] >> (idx & 31)) & 1
     return vals
 
 

@@ -25,7 +25,8 @@
  *     2^32-1, for j < l-1; T_{l-1} = 2^32.  The category of u is the number of
  *     values in (P32, T_0, .., T_{l-2}) that are <= u: category 0 means the
  *     node is perturbed (gamma_i = 1), category j+1 selects function j.
- *   - Truth table: value = bit (sum_m s[parent_m] << m) of the function's word.
+ *   - Truth table: value = bit j = (sum_m s[parent_m] << m) of the function's
+ *     table, stored as words: bit j % 32 of word j / 32 (k <= 12 parents).
  *   - Perturbation reading PER_NODE (mode 0): a perturbed node flips, every
  *     other node takes its selected function's value.  Reading GLOBAL (mode 1):
  *     if any node is perturbed the next state is s XOR gamma, else every node
@@ -42,6 +43,7 @@
 #define ORC_ERR_INVALID 1
 #define ORC_ERR_OOM 2
 #define ORC_ERR_NOT_CONVERGED 5
+#define ORC_MAX_PARENTS 12
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10, from the round function and key schedule published in       */
@@ -76,7 +78,8 @@ typedef struct {
     const int32_t *fn_offset;   /* [n+1] */
     const int32_t *par_offset;  /* [F+1] */
     const int32_t *parents;     /* [par_offset[F]] */
-    const uint32_t *truth_table;/* [F] */
+    const int32_t *tt_offset;   /* [F+1] truth-table words of function f: tt_offset[f] .. tt_offset[f+1]-1 */
+    const uint32_t *tt_words;   /* bit j of a table is bit j % 32 of its word j / 32 */
     const double *select_prob;  /* [F] */
     double p;
 } orc_net;
@@ -99,7 +102,9 @@ int orc_validate(const orc_net *net) {
     if (net->par_offset[0] != 0) return ORC_ERR_INVALID;
     for (int f = 0; f < net->F; f++) {
         int k = net->par_offset[f + 1] - net->par_offset[f];
-        if (k < 0 || k > 5) return ORC_ERR_INVALID;
+        if (k < 0 || k > ORC_MAX_PARENTS) return ORC_ERR_INVALID;
+        int words = (1 << k) / 32 > 1 ? (1 << k) / 32 : 1;
+        if (net->tt_offset[f + 1] - net->tt_offset[f] != words) return ORC_ERR_INVALID;
         for (int m = 0; m < k; m++) {
             int v = net->parents[net->par_offset[f] + m];
             if (v < 0 || v >= net->n) return ORC_ERR_INVALID;
@@ -196,7 +201,7 @@ static int eval_fn(const orc_net *net, int f, const uint8_t *s) {
     uint32_t idx = 0;
     int k = net->par_offset[f + 1] - net->par_offset[f];
     for (int m = 0; m < k; m++) idx |= (uint32_t)s[net->parents[net->par_offset[f] + m]] << m;
-    return (int)((net->truth_table[f] >> idx) & 1u);
+    return (int)((net->tt_words[net->tt_offset[f] + (idx >> 5)] >> (idx & 31u)) & 1u);
 }
 
 static int indicator(const uint8_t *s, const int32_t *soi_nodes, const uint8_t *soi_values, int soi_size) {

@@ -15,8 +15,13 @@ Network format (the PBN G(V, F) of Sec. 2.2, in CSR form):
                    ``parents[par_offset[f] : par_offset[f+1]]``
 * ``parents``      int32[sum k]; node indices, parent m is bit m of the
                    truth-table index
-* ``truth_table``  uint32[F]; value of f on parent values (x_0..x_{k-1}) is
-                   bit (sum_m x_m 2^m) of the word (k <= 5)
+* ``tt_offset``    int32[F+1]; function f's truth table is the words
+                   ``tt_words[tt_offset[f] : tt_offset[f+1]]``, max(1, 2^k / 32)
+                   of them; the value of f on parent values (x_0..x_{k-1}) is
+                   bit j % 32 of word j / 32, j = sum_m x_m 2^m (k <= 12)
+* ``tt_words``     uint32[...]
+* ``truth_table``  uint32[F]; each function's first word (its whole table
+                   when k <= 5)
 * ``select_prob``  float64[F]; selection probabilities c_j^(i), summing to 1
                    over the functions of each node
 * ``p``            perturbation probability
@@ -45,6 +50,16 @@ class PBN:
     select_prob: np.ndarray
     p: float
     name: str = ""
+    tt_offset: Optional[np.ndarray] = None
+    tt_words: Optional[np.ndarray] = None
+
+    def __post_init__(self):
+        if self.tt_offset is None:  # one word per function (every k <= 5)
+            self.tt_offset = np.arange(len(self.truth_table) + 1, dtype=np.int32)
+            self.tt_words = np.asarray(self.truth_table, dtype=np.uint32).copy()
+
+    def tt_of(self, f: int) -> np.ndarray:
+        return self.tt_words[self.tt_offset[f]:self.tt_offset[f + 1]]
 
     @property
     def n_functions(self) -> int:
@@ -73,6 +88,17 @@ class StateOfInterest:
         self.values = np.asarray(self.values, dtype=np.uint8)
 
 
+def tt_words_of(tt, k: int) -> np.ndarray:
+    """A truth table (Python int, or an array of 2^k bits) as max(1, 2^k/32)
+    uint32 words, bit j of the table at bit j % 32 of word j / 32."""
+    nw = max(1, (1 << k) >> 5)
+    if isinstance(tt, (int, np.integer)):
+        return np.array([(int(tt) >> (32 * w)) & 0xFFFFFFFF for w in range(nw)], dtype=np.uint32)
+    bits = np.zeros(nw * 32, dtype=np.uint64)
+    bits[:len(tt)] = np.asarray(tt, dtype=np.uint64)
+    return (bits.reshape(nw, 32) << np.arange(32, dtype=np.uint64)).sum(axis=1).astype(np.uint32)
+
+
 def _assemble(n, fn_counts, fn_parents, fn_tts, fn_probs, p, name) -> PBN:
     fn_offset = np.zeros(n + 1, dtype=np.int32)
     fn_offset[1:] = np.cumsum(fn_counts)
@@ -81,10 +107,15 @@ def _assemble(n, fn_counts, fn_parents, fn_tts, fn_probs, p, name) -> PBN:
     par_offset[1:] = np.cumsum([len(x) for x in fn_parents])
     parents = (np.concatenate([np.asarray(x, dtype=np.int32) for x in fn_parents])
                if F and par_offset[-1] else np.zeros(0, dtype=np.int32))
+    words = [tt_words_of(tt, len(par)) for tt, par in zip(fn_tts, fn_parents)]
+    tt_offset = np.zeros(F + 1, dtype=np.int32)
+    tt_offset[1:] = np.cumsum([len(w) for w in words])
+    tt_words = np.concatenate(words) if words else np.zeros(0, dtype=np.uint32)
     return PBN(n=n, fn_offset=fn_offset, par_offset=par_offset,
                parents=parents.astype(np.int32),
-               truth_table=np.asarray(fn_tts, dtype=np.uint32),
-               select_prob=np.asarray(fn_probs, dtype=np.float64), p=float(p), name=name)
+               truth_table=np.array([w[0] for w in words], dtype=np.uint32),
+               select_prob=np.asarray(fn_probs, dtype=np.float64), p=float(p), name=name,
+               tt_offset=tt_offset, tt_words=tt_words.astype(np.uint32))
 
 
 def random_pbn(seed: int, n: int, fn_range=(1, 3), par_range=(1, 3),
@@ -125,11 +156,8 @@ def random_pbn(seed: int, n: int, fn_range=(1, 3), par_range=(1, 3),
             else:
                 q = rng.uniform(0.3, 0.7)
                 bits = (rng.random(1 << k) < q).astype(np.int64)
-            tt = 0
-            for b, v in enumerate(bits):
-                tt |= int(v) << b
             fn_parents.append(par)
-            fn_tts.append(tt)
+            fn_tts.append(bits)
             fn_probs.append(float(probs[j]))
     return _assemble(n, fn_counts, fn_parents, fn_tts, fn_probs, p, name)
 
