@@ -57,7 +57,7 @@ enum { PBN_PERTURB_PER_NODE = 0, PBN_PERTURB_GLOBAL = 1 };
 
 /* Limits of this build. */
 #define PBN_MAX_NODES 4096          /* node ids are 12-bit in the device tables */
-#define PBN_MAX_PARENTS 5           /* truth tables are one 32-bit word */
+#define PBN_MAX_PARENTS 12          /* truth tables up to 4096 bits (128 words) */
 #define PBN_MAX_FUNCTIONS_PER_NODE 8
 #define PBN_MAX_SOI 32               /* state-of-interest entries of one run, over all its properties */
 #define PBN_MAX_PROPERTIES 8         /* properties abstracted from one set of trajectories (Sec. 4.2) */
@@ -77,9 +77,14 @@ typedef struct pbn_network_desc {
     const int32_t *fn_offset;
     const int32_t *par_offset;
     const int32_t *parents;
-    const uint32_t *truth_table;
+    const uint32_t *truth_table;   /* one word per function (used when tt_offset is NULL; then k <= 5) */
     const double *select_prob;
     double p;
+    /* Truth tables of any size up to PBN_MAX_PARENTS inputs (may be NULL):
+     * function f's table is tt_words[tt_offset[f] .. tt_offset[f+1]-1],
+     * max(1, 2^k / 32) words; bit j of the table is bit j % 32 of word j / 32. */
+    const int32_t *tt_offset;
+    const uint32_t *tt_words;
 } pbn_network_desc;
 
 typedef struct pbn_net pbn_net;

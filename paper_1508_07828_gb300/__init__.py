@@ -48,7 +48,8 @@ c_i32, c_i64, c_u32, c_u64, c_dbl, c_vp = (ctypes.c_int32, ctypes.c_int64, ctype
 
 class NetworkDesc(ctypes.Structure):
     _fields_ = [("n", c_i32), ("n_functions", c_i32), ("fn_offset", c_vp), ("par_offset", c_vp),
-                ("parents", c_vp), ("truth_table", c_vp), ("select_prob", c_vp), ("p", c_dbl)]
+                ("parents", c_vp), ("truth_table", c_vp), ("select_prob", c_vp), ("p", c_dbl),
+                ("tt_offset", c_vp), ("tt_words", c_vp)]
 
 
 class NetInfo(ctypes.Structure):
@@ -233,10 +234,15 @@ class Network:
             parents=np.ascontiguousarray(net.parents if len(net.parents) else np.zeros(1, np.int32), dtype=np.int32),
             truth_table=np.ascontiguousarray(net.truth_table, dtype=np.uint32),
             select_prob=np.ascontiguousarray(net.select_prob, dtype=np.float64))
+        wide = getattr(net, "tt_offset", None) is not None
+        if wide:
+            self._arrays["tt_offset"] = np.ascontiguousarray(net.tt_offset, dtype=np.int32)
+            self._arrays["tt_words"] = np.ascontiguousarray(net.tt_words, dtype=np.uint32)
         a = self._arrays
         desc = NetworkDesc(int(net.n), int(a["fn_offset"][-1]), a["fn_offset"].ctypes.data, a["par_offset"].ctypes.data,
                            a["parents"].ctypes.data, a["truth_table"].ctypes.data, a["select_prob"].ctypes.data,
-                           float(net.p))
+                           float(net.p), a["tt_offset"].ctypes.data if wide else None,
+                           a["tt_words"].ctypes.data if wide else None)
         h = c_vp()
         _check(lib().pbn_load(ctypes.byref(desc), ctypes.byref(h)))
         self.handle = h
@@ -266,13 +272,16 @@ def pbn_load(net) -> Network:
 
 def pbn_load_pinned(host_arrays: dict, n: int, p: float) -> Network:
     """Stage a network whose CSR arrays are pinned host tensors (keys
-    fn_offset, par_offset, parents, truth_table, select_prob): pbn_load then
-    copies them to the device from page-locked memory."""
+    fn_offset, par_offset, parents, truth_table, select_prob, and optionally
+    tt_offset, tt_words): pbn_load then copies them to the device from
+    page-locked memory."""
     self = Network.__new__(Network)
     self._arrays = host_arrays
     a = host_arrays
     desc = NetworkDesc(int(n), int(a["fn_offset"][-1]), a["fn_offset"].data_ptr(), a["par_offset"].data_ptr(),
-                       a["parents"].data_ptr(), a["truth_table"].data_ptr(), a["select_prob"].data_ptr(), float(p))
+                       a["parents"].data_ptr(), a["truth_table"].data_ptr(), a["select_prob"].data_ptr(), float(p),
+                       a["tt_offset"].data_ptr() if "tt_offset" in a else None,
+                       a["tt_words"].data_ptr() if "tt_words" in a else None)
     h = c_vp()
     _check(lib().pbn_load(ctypes.byref(desc), ctypes.byref(h)))
     self.handle = h

@@ -136,8 +136,10 @@ int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, in
     gpb = std::max(1, gpb / 2);
   }
   int T = T_req;
-  if (T == 0) T = (G < sm_count() && net.n * gpb * 2 <= 512) ? 2 : 1;
+  if (T == 0) T = (G < sm_count() && net.n * gpb * 2 <= 512 && !net.has_wide) ? 2 : 1;
   if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
+  if (net.has_wide && (T != 1 || (BPR_req && BPR_req != 1)))
+    return fail(PBN_ERR_UNSUPPORTED, "functions with more than 5 inputs run one thread per item, one block per round");
   int BPR = BPR_req ? BPR_req : 1;
   if (T == 2) BPR = 2;
   if (T == 4) BPR = 1;
@@ -177,6 +179,9 @@ pbn::SimArgs make_args(const pbn::NetDev &net, const pbn_run_cfg &cfg, const pbn
   a.tiles = net.d_tiles;
   a.ntiles = net.ntiles;
   a.tile_bytes = net.tile_bytes;
+  a.wide_tt = net.d_wide_tt;
+  a.wide_par = net.d_wide_par;
+  a.has_wide = net.has_wide;
   a.status = pbn::device_status();
   {
     static const int stall = getenv("PBN_TEST_STALL_FIRST_TILE") ? atoi(getenv("PBN_TEST_STALL_FIRST_TILE")) : 0;
@@ -296,8 +301,10 @@ int plan_select(const pbn::NetDev &net, int64_t omega, int gpb_req, int threads_
   // operations, so spreading it over more warps pays), 1 beyond (there extra
   // threads only multiply the work of the generic path).  Measured on GB300
   // over n = 100 .. 3000 with 256 .. 4096 chains.
-  const int T = T_req > 0 ? T_req : (net.n * gpb <= 300 ? 2 : 1);
+  const int T = T_req > 0 ? T_req : (net.n * gpb <= 300 && !net.has_wide ? 2 : 1);
   if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
+  if (net.has_wide && T != 1)
+    return fail(PBN_ERR_UNSUPPORTED, "functions with more than 5 inputs run one thread per item");
   const int items = net.n * gpb;
   const int tmax = pbn::apply_threads_limit(T);
   // with T > 1 and one item per T threads, one more warp feeds the others
@@ -481,6 +488,9 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
   std::vector<uint4> fn(F);
   std::vector<uint32_t> node(n);
   std::vector<std::pair<uint64_t, int>> order(n);
+  // tables of functions with more than 5 inputs, and their parents
+  std::vector<uint32_t> wide_tt;
+  std::vector<uint16_t> wide_par;
   int max_l = 0;
   for (int i = 0; i < n; i++) {
     const int f0 = d->fn_offset[i], f1 = d->fn_offset[i + 1];
@@ -498,12 +508,22 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
       const int k = d->par_offset[f + 1] - d->par_offset[f];
       if (k < 0) return fail(PBN_ERR_INVALID, "par_offset decreasing at %d", f);
       if (k > PBN_MAX_PARENTS) return fail(PBN_ERR_UNSUPPORTED, "function %d has %d parents", f, k);
-      shape = shape * 8 + (uint64_t)k;
-      int par[5] = {0, 0, 0, 0, 0};
+      shape = shape * 16 + (uint64_t)k;
       for (int m = 0; m < k; m++) {
         const int v = d->parents[d->par_offset[f] + m];
         if (v < 0 || v >= n) return fail(PBN_ERR_INVALID, "parent %d out of range", v);
-        par[m] = v;
+      }
+      const int words = k > 5 ? 1 << (k - 5) : 1;
+      const uint32_t *tt;
+      if (d->tt_offset) {
+        if (!d->tt_words) return fail(PBN_ERR_INVALID, "tt_words is NULL");
+        if (d->tt_offset[f + 1] - d->tt_offset[f] != words)
+          return fail(PBN_ERR_INVALID, "function %d: %d table words for %d inputs (need %d)", f,
+                      d->tt_offset[f + 1] - d->tt_offset[f], k, words);
+        tt = d->tt_words + d->tt_offset[f];
+      } else {
+        if (k > 5) return fail(PBN_ERR_INVALID, "function %d has %d inputs: its table needs tt_offset/tt_words", f, k);
+        tt = d->truth_table + f;
       }
       // upper category bound of function f (the last one of a node is 2^32, never compared)
       uint32_t T = 0xFFFFFFFFu;
@@ -516,11 +536,22 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
         T = t > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)t;
       }
       uint4 r;
-      // bits at or above 2^k are not part of the function; the kernels rely on them being 0
-      r.x = k == 5 ? d->truth_table[f] : (d->truth_table[f] & ((1u << (1u << k)) - 1u));
       r.y = T;
-      r.z = (uint32_t)par[0] | ((uint32_t)par[1] << 12) | (((uint32_t)par[4] & 0xFFu) << 24);
-      r.w = (uint32_t)par[2] | ((uint32_t)par[3] << 12) | (((uint32_t)par[4] >> 8) << 24) | ((uint32_t)k << 28);
+      if (k <= 5) {
+        int par[5] = {0, 0, 0, 0, 0};
+        for (int m = 0; m < k; m++) par[m] = d->parents[d->par_offset[f] + m];
+        // bits at or above 2^k are not part of the function; the kernels rely on them being 0
+        r.x = k == 5 ? tt[0] : (tt[0] & ((1u << (1u << k)) - 1u));
+        r.z = (uint32_t)par[0] | ((uint32_t)par[1] << 12) | (((uint32_t)par[4] & 0xFFu) << 24);
+        r.w = (uint32_t)par[2] | ((uint32_t)par[3] << 12) | (((uint32_t)par[4] >> 8) << 24) | ((uint32_t)k << 28);
+      } else {
+        // wide function: x = first table word in wide_tt, z = first parent in wide_par
+        r.x = (uint32_t)wide_tt.size();
+        r.z = (uint32_t)wide_par.size();
+        r.w = (uint32_t)k << 28;
+        wide_tt.insert(wide_tt.end(), tt, tt + words);
+        for (int m = 0; m < k; m++) wide_par.push_back((uint16_t)d->parents[d->par_offset[f] + m]);
+      }
       fn[f] = r;
     }
     if (fabs(sum - 1.0) > 1e-9) return fail(PBN_ERR_INVALID, "selection probabilities of node %d sum to %.17g", i, sum);
@@ -573,11 +604,21 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
     e = cudaMemcpy(net->dev.d_node, node_sorted.data(), sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(net->dev.d_tiles, tiles.data(), sizeof(int32_t) * tiles.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !wide_tt.empty()) {
+    net->dev.has_wide = 1;
+    e = cudaMalloc(&net->dev.d_wide_tt, sizeof(uint32_t) * wide_tt.size());
+    if (e == cudaSuccess) e = cudaMalloc(&net->dev.d_wide_par, sizeof(uint16_t) * wide_par.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(net->dev.d_wide_tt, wide_tt.data(), sizeof(uint32_t) * wide_tt.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(net->dev.d_wide_par, wide_par.data(), sizeof(uint16_t) * wide_par.size(),
+                     cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     pbn_free(net);
     return cuda_fail(e, "staging network tables");
   }
-  net->dev.table_bytes = (int64_t)F * 16 + (int64_t)n * 4;
+  net->dev.table_bytes = (int64_t)F * 16 + (int64_t)n * 4 + (int64_t)wide_tt.size() * 4 + (int64_t)wide_par.size() * 2;
   *out = net;
   return PBN_OK;
 }
@@ -587,6 +628,8 @@ void pbn_free(pbn_net *net) {
   if (net->dev.d_fn) cudaFree(net->dev.d_fn);
   if (net->dev.d_node) cudaFree(net->dev.d_node);
   if (net->dev.d_tiles) cudaFree(net->dev.d_tiles);
+  if (net->dev.d_wide_tt) cudaFree(net->dev.d_wide_tt);
+  if (net->dev.d_wide_par) cudaFree(net->dev.d_wide_par);
   delete net;
 }
 

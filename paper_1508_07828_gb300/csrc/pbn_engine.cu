@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(512) batch_sim_kernel(const SimArgs *__restric
     __syncthreads();
     const RoundKeys rk = s_task.rk;
     if (s_task.mode == PBN_PERTURB_PER_NODE)
-      cta_simulate<PBN_PERTURB_PER_NODE, 1, 1>(s_task, rk, (uint32_t)w.g0, w.ngl, smem);
+      cta_simulate<PBN_PERTURB_PER_NODE, 1, 1, true>(s_task, rk, (uint32_t)w.g0, w.ngl, smem);
     else
-      cta_simulate<PBN_PERTURB_GLOBAL, 1, 1>(s_task, rk, (uint32_t)w.g0, w.ngl, smem);
+      cta_simulate<PBN_PERTURB_GLOBAL, 1, 1, true>(s_task, rk, (uint32_t)w.g0, w.ngl, smem);
     __syncthreads();
   }
 }
@@ -816,6 +816,9 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       a.tiles = d.d_tiles;
       a.ntiles = d.ntiles;
       a.tile_bytes = d.tile_bytes;
+      a.wide_tt = d.d_wide_tt;
+      a.wide_par = d.d_wide_par;
+      a.has_wide = d.has_wide;
       a.status = e->status;
       a.soi_size = (int)q.soi_nodes.size();
       a.n_props = 1;  // one property per engine query (soi_prop all 0)

@@ -14,11 +14,13 @@ constexpr int kMaxProps = PBN_MAX_PROPERTIES;
 
 // Device tables of one network (built by pbn_load).
 //  node record (processing order r):  bits 0-11 node id, 12-15 l-1, 16-31 first function
-//  function record (uint4):
+//  function record (uint4), k <= 5 inputs:
 //    x = truth table
 //    y = upper category bound T_j (unused for the last function of a node)
 //    z = p0 | p1 << 12 | (p4 & 0xFF) << 24
 //    w = p2 | p3 << 12 | (p4 >> 8) << 24 | k << 28
+//  k = 6 .. 12 inputs ("wide"): x = first of its 2^(k-5) table words in
+//    d_wide_tt, z = first of its k parents in d_wide_par, w = k << 28
 struct NetDev {
   int n = 0, F = 0;
   uint32_t P32 = 0;
@@ -29,6 +31,9 @@ struct NetDev {
   int ntiles = 0;
   int tile_bytes = 0;             // largest tile
   int64_t table_bytes = 0;
+  int has_wide = 0;               // some function has more than 5 inputs
+  uint32_t *d_wide_tt = nullptr;  // their truth tables (record x = first word)
+  uint16_t *d_wide_par = nullptr; // their parents (record z = first entry)
 };
 
 // Records per TMA tile (24 KB of function records).
@@ -101,6 +106,9 @@ struct SimArgs {
   uint16_t soi_node[kMaxSoi];
   uint32_t soi_val;      // bit m = required value of soi_node[m]
   int mode;              // perturbation reading (batched kernel only)
+  const uint32_t *wide_tt;   // tables and parents of functions with more than 5 inputs (NetDev)
+  const uint16_t *wide_par;
+  int has_wide;
   int W;                 // select-ahead: category words per (step, group), F rounded up to 4
   uint32_t *planes;      // select-ahead: category words [steps][G][W] of the chunk
   uint32_t *anyw;        // select-ahead, global perturbation: [steps][G] OR of the perturbed lanes

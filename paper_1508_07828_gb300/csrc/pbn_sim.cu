@@ -33,11 +33,13 @@
 
 namespace pbn {
 
-template <int MODE, int T, int BPR>
+// WIDE: the variant for networks with functions of more than 5 inputs (one
+// thread per item, one Philox block per round only).
+template <int MODE, int T, int BPR, bool WIDE>
 __global__ void __launch_bounds__(max_threads<T>()) sim_kernel(const __grid_constant__ SimArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t g0 = blockIdx.x * (uint32_t)a.gpb;
-  cta_simulate<MODE, T, BPR>(a, a.rk, g0, min(a.gpb, a.G - (int)g0), smem);
+  cta_simulate<MODE, T, BPR, WIDE>(a, a.rk, g0, min(a.gpb, a.G - (int)g0), smem);
 }
 
 __global__ void init_kernel(const __grid_constant__ RoundKeys rk, uint32_t *state, int n, int G, int64_t omega) {
@@ -86,22 +88,26 @@ int sim_max_smem() {
   return v;
 }
 
-template <int MODE, int T, int BPR>
+template <int MODE, int T, int BPR, bool WIDE = false>
 static cudaError_t launch_variant(const SimArgs &a, int blocks, int threads, size_t smem, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(sim_kernel<MODE, T, BPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(sim_kernel<MODE, T, BPR, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          sim_max_smem());
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  sim_kernel<MODE, T, BPR><<<blocks, threads, smem, s>>>(a);
+  sim_kernel<MODE, T, BPR, WIDE><<<blocks, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int MODE>
 static cudaError_t launch_mode(const SimArgs &a, int T, int BPR, int blocks, int threads, size_t smem,
                                cudaStream_t s) {
+  if (a.has_wide) {
+    if (T != 1 || BPR != 1) return cudaErrorInvalidValue;  // the planner gives wide networks T = 1, BPR = 1
+    return launch_variant<MODE, 1, 1, true>(a, blocks, threads, smem, s);
+  }
   if (T == 4) return launch_variant<MODE, 4, 1>(a, blocks, threads, smem, s);
   if (T == 2) return launch_variant<MODE, 2, 2>(a, blocks, threads, smem, s);
   if (BPR == 1) return launch_variant<MODE, 1, 1>(a, blocks, threads, smem, s);

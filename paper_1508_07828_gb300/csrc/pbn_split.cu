@@ -225,8 +225,8 @@ int apply_threads_limit(int T) { return T == 2 ? apply_max_threads<2>() : apply_
 
 // One CTA per `gpb` chain groups applies a.steps steps of category words;
 // T threads per (node, group) item.
-template <int MODE, int kRing, int T>
-__global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __grid_constant__ SimArgs a) {
+template <int MODE, int kRing, int T, bool WIDE>
+__global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const __grid_constant__ SimArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gpb = a.gpb, n = a.n, W = a.W;
   const uint32_t g0 = blockIdx.x * (uint32_t)gpb;
@@ -238,11 +238,12 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
   const uint4 *fn_s = a.fn;
   const bool tt_replicated = a.staging == STAGE_SMEM;
   if (tt_replicated) {
-    // the shared copy carries every truth table already replicated to 32 leaves
+    // the shared copy carries every truth table already replicated to 32
+    // leaves (wide records keep their table offset)
     uint4 *f = reinterpret_cast<uint4 *>(p);
     for (int j = threadIdx.x; j < a.F; j += blockDim.x) {
       uint4 r = a.fn[j];
-      r.x = replicate5(r.x, fn_k(r));
+      if (fn_k(r) <= 5) r.x = replicate5(r.x, fn_k(r));
       f[j] = r;
     }
     fn_s = f;
@@ -317,14 +318,21 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
       rest &= ~sel;
       const bool has = sel != 0u;  // the same in the T threads of an item
       if (__any_sync(kFull, has)) {
-        const uint4 fr = has ? fn_s[f0 + j] : make_uint4(0u, 0u, 0u, 0u);
+        uint4 fr = has ? fn_s[f0 + j] : make_uint4(0u, 0u, 0u, 0u);
+        bool wide = false;
+        if (WIDE && a.has_wide) {  // kernel-uniform: the item's first thread asks the warp for a wide function
+          wide = fn_k(fr) > 5;
+          fword |= sel & eval_wide_warp(wide && sub == 0, fr, cur, gpb, gl, a.wide_tt, a.wide_par);
+          if (wide) fr = make_uint4(0u, 0u, 0u, 0u);
+        }
         const int pr[5] = {(int)(fr.z & 0xFFF), (int)((fr.z >> 12) & 0xFFF), (int)(fr.w & 0xFFF),
                            (int)((fr.w >> 12) & 0xFFF), (int)((fr.z >> 24) | (((fr.w >> 24) & 0xFu) << 8))};
         uint32_t x[5];
 #pragma unroll
         for (int m = 0; m < 5; m++) x[m] = cur[pr[m] * gpb + gl];
         const uint32_t tt5 = tt_replicated ? fr.x : replicate5(fr.x, fn_k(fr));
-        fword |= sel & eval5_shared<T>(tt5, x, sub);
+        const uint32_t v = eval5_shared<T>(tt5, x, sub);
+        if (!wide) fword |= sel & v;
       }
     }
   };
@@ -339,7 +347,7 @@ __global__ void __launch_bounds__(apply_max_threads<T>()) apply_kernel(const __g
     nxt[idx] = v;
     return v;
   };
-  if (T > 1 && items * T <= (int)blockDim.x - 32) {
+  if (!WIDE && T > 1 && items * T <= (int)blockDim.x - 32) {
     // One item per T threads for the whole launch, everything that does not
     // change from step to step in registers; the last warp is the producer:
     // it waits for the category words, writes the indicator and requests the
@@ -498,21 +506,25 @@ cudaError_t launch_select(const SimArgs &a, int mode, int BPR, cudaStream_t s) {
                   : launch_select_variant<PBN_PERTURB_GLOBAL, 1>(a, s);
 }
 
-template <int MODE, int RING, int T>
+template <int MODE, int RING, int T, bool WIDE = false>
 static cudaError_t launch_apply_variant(const SimArgs &a, int blocks, int threads, size_t smem, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(apply_kernel<MODE, RING, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         sim_max_smem());
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel<MODE, RING, T, WIDE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sim_max_smem());
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  apply_kernel<MODE, RING, T><<<blocks, threads, smem, s>>>(a);
+  apply_kernel<MODE, RING, T, WIDE><<<blocks, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
+// Networks with functions of more than 5 inputs run the generic loop with one
+// thread per item (the planner gives them T = 1).
 template <int MODE, int RING>
 static cudaError_t launch_apply_ring(const SimArgs &a, int T, int blocks, int threads, size_t smem, cudaStream_t s) {
+  if (a.has_wide) return T == 1 ? launch_apply_variant<MODE, RING, 1, true>(a, blocks, threads, smem, s)
+                                : cudaErrorInvalidValue;
   if (T == 4) return launch_apply_variant<MODE, RING, 4>(a, blocks, threads, smem, s);
   if (T == 2) return launch_apply_variant<MODE, RING, 2>(a, blocks, threads, smem, s);
   return launch_apply_variant<MODE, RING, 1>(a, blocks, threads, smem, s);

@@ -68,8 +68,41 @@ __device__ __forceinline__ uint32_t eval_uniform(int K, uint4 rec, int k, const 
   }
 }
 
+// Functions with more than 5 inputs ("wide"): a multiplexer tree would have
+// 2^k leaves, so the warp looks the value up chain by chain instead.  For
+// every lane that asks (`mine`), in turn: its record and chain group are
+// broadcast, lane q gathers chain q's table index from the k parents' state
+// words (bit q of each) and reads that bit of the table, and one ballot
+// collects the 32 chains' values for the asking lane.  All 32 lanes must call.
+static __device__ __noinline__ uint32_t eval_wide_warp(bool mine, uint4 rec, const uint32_t *cur, int gpb, int gl,
+                                                   const uint32_t *wide_tt, const uint16_t *wide_par) {
+  const int lane = threadIdx.x & 31;
+  uint32_t result = 0u;
+  unsigned pend = __ballot_sync(kFull, mine);
+  while (pend) {
+    const int src = __ffs(pend) - 1;
+    pend &= pend - 1;
+    const uint32_t tt0 = __shfl_sync(kFull, rec.x, src);
+    const uint32_t p0 = __shfl_sync(kFull, rec.z, src);
+    const int k = (int)(__shfl_sync(kFull, rec.w, src) >> 28);
+    const int g = __shfl_sync(kFull, gl, src);
+    uint32_t idx = 0u;
+    for (int m = 0; m < k; m++) {
+      const uint32_t w = cur[(int)wide_par[p0 + m] * gpb + g];  // one address for the whole warp
+      idx |= ((w >> lane) & 1u) << m;
+    }
+    const uint32_t bit = (wide_tt[tt0 + (idx >> 5)] >> (idx & 31u)) & 1u;
+    const uint32_t v = __ballot_sync(kFull, bit != 0u);
+    if (lane == src) result = v;
+  }
+  return result;
+}
+
 struct ItemCtx {
   const uint4 *fn_s;
+  const uint32_t *wide_tt;
+  const uint16_t *wide_par;
+  int has_wide;
   const uint32_t *cur;
   uint32_t *nxt;
   uint32_t *pbuf;
@@ -164,7 +197,9 @@ __device__ __forceinline__ void select_masks(const uint32_t (&lt)[LW], uint32_t 
 }
 
 // One item of one transition: category draw, then the selected functions.
-template <int LW, int MODE, int T, int BPR>
+// WIDE: compiled with the lookup of functions with more than 5 inputs (used
+// when c.has_wide); without it the code is the common path alone.
+template <int LW, int MODE, int T, int BPR, bool WIDE>
 __device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
   uint32_t lt[LW];
   draw_below<LW, T, BPR>(rk, P32, c, lt);
@@ -181,8 +216,17 @@ __device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, con
     const bool has = (j < c.L) && my_sel != 0u;
     const uint4 rec = has ? c.fn_s[c.f0 + j] : make_uint4(0u, 0u, 0u, 0u);
     const int k = has ? fn_k(rec) : 0;
-    const int K = __reduce_max_sync(kFull, (unsigned)k);
-    if (__any_sync(kFull, has)) fword |= my_sel & eval_uniform(K, rec, k, c.cur, c.gpb, c.gl);
+    if (WIDE && c.has_wide) {  // kernel-uniform
+      const bool wide = k > 5;
+      const uint4 tr = wide ? make_uint4(0u, 0u, 0u, 0u) : rec;
+      const int kt = wide ? 0 : k;
+      const int K = __reduce_max_sync(kFull, (unsigned)kt);
+      if (__any_sync(kFull, has && !wide)) fword |= (wide ? 0u : my_sel) & eval_uniform(K, tr, kt, c.cur, c.gpb, c.gl);
+      fword |= my_sel & eval_wide_warp(wide, rec, c.cur, c.gpb, c.gl, c.wide_tt, c.wide_par);
+    } else {
+      const int K = __reduce_max_sync(kFull, (unsigned)k);
+      if (__any_sync(kFull, has)) fword |= my_sel & eval_uniform(K, rec, k, c.cur, c.gpb, c.gl);
+    }
   }
 #pragma unroll
   for (int k = 1; k < T; k <<= 1) fword |= __shfl_xor_sync(kFull, fword, k);
@@ -205,20 +249,20 @@ __device__ __forceinline__ uint32_t lane_mask(int64_t omega, uint32_t g) {
 
 // Nodes with more than 4 functions are rare; their variant is kept out of
 // line so its register demand does not raise the common path's.
-template <int MODE, int T, int BPR>
+template <int MODE, int T, int BPR, bool WIDE>
 __device__ __noinline__ void step_item_wide(const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
-  step_item<kMaxL, MODE, T, BPR>(rk, P32, c);
+  step_item<kMaxL, MODE, T, BPR, WIDE>(rk, P32, c);
 }
 
-template <int MODE, int T, int BPR>
+template <int MODE, int T, int BPR, bool WIDE>
 __device__ __forceinline__ void dispatch_item(int LW, const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
   switch (LW) {
     case 0: break;
-    case 1: step_item<1, MODE, T, BPR>(rk, P32, c); break;
-    case 2: step_item<2, MODE, T, BPR>(rk, P32, c); break;
-    case 3: step_item<3, MODE, T, BPR>(rk, P32, c); break;
-    case 4: step_item<4, MODE, T, BPR>(rk, P32, c); break;
-    default: step_item_wide<MODE, T, BPR>(rk, P32, c); break;
+    case 1: step_item<1, MODE, T, BPR, WIDE>(rk, P32, c); break;
+    case 2: step_item<2, MODE, T, BPR, WIDE>(rk, P32, c); break;
+    case 3: step_item<3, MODE, T, BPR, WIDE>(rk, P32, c); break;
+    case 4: step_item<4, MODE, T, BPR, WIDE>(rk, P32, c); break;
+    default: step_item_wide<MODE, T, BPR, WIDE>(rk, P32, c); break;
   }
 }
 
@@ -277,7 +321,7 @@ constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: a 24 KB tile arrives i
 // Function records come from shared memory (whole tables), from TMA tiles
 // streamed through two shared buffers (tile u of the launch's sequence
 // s*ntiles + t goes to buffer u & 1), or straight from global memory.
-template <int MODE, int T, int BPR>
+template <int MODE, int T, int BPR, bool WIDE>
 __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &rk, uint32_t g0, int ngl,
                                              unsigned char *smem) {
   const int gpb = a.gpb;
@@ -356,6 +400,9 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
   uint32_t *cur = bufA, *nxt = bufB;
   for (int s = 0; s < a.steps; s++) {
     ItemCtx c;
+    c.wide_tt = a.wide_tt;
+    c.wide_par = a.wide_par;
+    c.has_wide = a.has_wide;
     c.cur = cur;
     c.nxt = nxt;
     c.pbuf = pbuf;
@@ -394,7 +441,7 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
         c.g = g0 + (uint32_t)c.gl;
         c.vmask = c.active ? lane_mask(a.omega, c.g) : 0u;
         const int LW = (int)__reduce_max_sync(kFull, (unsigned)c.L);
-        dispatch_item<MODE, T, BPR>(LW, rk, P32, c);
+        dispatch_item<MODE, T, BPR, WIDE>(LW, rk, P32, c);
       }
       __syncthreads();
       if (staging == STAGE_TILES && threadIdx.x == 0) {

@@ -46,7 +46,7 @@ def test_status_strings_and_error_channel():
 
 STRUCTS = {
     "NetworkDesc": ("pbn_network_desc", ["n", "n_functions", "fn_offset", "par_offset", "parents", "truth_table",
-                                         "select_prob", "p"]),
+                                         "select_prob", "p", "tt_offset", "tt_words"]),
     "NetInfo": ("pbn_net_info", ["n", "n_functions", "perturb_threshold", "table_bytes"]),
     "Soi": ("pbn_soi", ["size", "nodes", "values"]),
     "Chains": ("pbn_chains", ["omega", "state", "bits", "bits_cap", "bits_base", "length"]),
