@@ -66,6 +66,12 @@ def parse():
                     help="sequential Alg. 1 on one chain against the parallel query (speed-up, speed-up E)")
     ap.add_argument("--seq-r", type=float, default=1e-4,
                     help="precision r of the --seq comparison (the paper's experiments use 1e-4)")
+    ap.add_argument("--sweep", action="store_true", help="the paper's n x density sweep at precision --seq-r")
+    ap.add_argument("--sweep-omega", type=int, default=2048)
+    ap.add_argument("--sweep-seq-max-n", type=int, default=100)
+    ap.add_argument("--sweep-classes", default="sparse,in-between", help="density classes of --sweep")
+    ap.add_argument("--sweep-seq-classes", default="sparse",
+                    help="classes whose smallest models also run the sequential Alg. 1 (minutes per model otherwise)")
     ap.add_argument("--multi", type=int, default=0,
                     help="Q properties from the same trajectories against Q separate queries (mid workload)")
     ap.add_argument("--rates", default="50,200,1000,2000", help="arrival rates (queries/s) for --serve")
@@ -608,6 +614,48 @@ def run_seq(args):
                       "seq_length": med("len_seq"), "agreement_within_2r": agree}))
 
 
+def run_sweep(args):
+    """The paper's sweep (Sec. 5.1) in shape: n in {80, 100, 200, 500, 1000,
+    2000} x density classes (sparse ~10, in-between 50-100; synthetic models
+    from pbn_synth.sweep_config), two-state at precision r (1e-4 in the
+    paper) with --sweep-omega chains; for n <= --sweep-seq-max-n also the
+    sequential Alg. 1 (speed-up and speed-up E).  One JSON line per model."""
+    import torch
+    import pbn_synth as S
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+    torch.cuda.set_device(0)
+    r = args.seq_r
+    for density in [d for d in args.sweep_classes.split(",") if d in S.DENSITY_CLASSES]:
+        for n in (80, 100, 200, 500, 1000, 2000):
+            net, soi = S.sweep_config(n, density)
+            N = P.pbn_load(net)
+            kw = dict(omega=args.sweep_omega, psi0=PSI0, rhat=1.05, eps=1e-10, r=r, s=0.95,
+                      max_length=args.max_length)
+            row = {"mode": "sweep", "n": n, "density_class": density, "density": round(net.density(), 1),
+                   "functions": int(net.n_functions), "chains": args.sweep_omega, "r": r}
+            try:
+                P.pbn_estimate_two_state(N, soi, seed=1, **dict(kw, r=0.01))  # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rep = P.pbn_estimate_two_state(N, soi, seed=2, **kw)
+                tp = time.perf_counter() - t0
+                row.update({"t_par_s": tp, "length": rep["length"], "sample_size": rep["sample_size"],
+                            "prob": rep["prob"], "updates_per_s": rep["chain_node_updates"] / tp})
+                if n <= args.sweep_seq_max_n and density in args.sweep_seq_classes.split(","):
+                    t0 = time.perf_counter()
+                    sq = P.pbn_estimate_two_state_seq(N, soi, seed=3, m0=0, n0=PSI0, eps=1e-10, r=r, s=0.95)
+                    ts = time.perf_counter() - t0
+                    sp = ts / tp
+                    row.update({"t_seq_s": ts, "seq_size": sq["N"], "prob_seq": sq["prob"], "speedup": sp,
+                                "speedup_E": sp * rep["sample_size"] / sq["N"],
+                                "within_2r": abs(sq["prob"] - rep["prob"]) < 2 * r})
+            except P.PbnError as e:
+                row["error"] = str(e)
+            print(json.dumps(row), flush=True)
+
+
 def run_serve(args):
     """Serving: queries arrive as a Poisson process; each names a random
     network of the 200-network pool (n log-uniform in [20, 3000]), a state
@@ -687,6 +735,9 @@ def main():
         return
     if args.seq:
         run_seq(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if args.batched:
         run_batched(args)

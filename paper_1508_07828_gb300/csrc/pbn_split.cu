@@ -320,10 +320,12 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
       if (__any_sync(kFull, has)) {
         uint4 fr = has ? fn_s[f0 + j] : make_uint4(0u, 0u, 0u, 0u);
         bool wide = false;
-        if (WIDE && a.has_wide) {  // kernel-uniform: the item's first thread asks the warp for a wide function
+        if (WIDE && a.has_wide) {  // kernel-uniform (wide networks run T = 1)
           wide = fn_k(fr) > 5;
-          fword |= sel & eval_wide_warp(wide && sub == 0, fr, cur, gpb, gl, a.wide_tt, a.wide_par);
-          if (wide) fr = make_uint4(0u, 0u, 0u, 0u);
+          if (wide) {
+            fword |= eval_wide_lanes(fr, sel, cur, gpb, gl, a.wide_tt, a.wide_par);
+            fr = make_uint4(0u, 0u, 0u, 0u);
+          }
         }
         const int pr[5] = {(int)(fr.z & 0xFFF), (int)((fr.z >> 12) & 0xFFF), (int)(fr.w & 0xFFF),
                            (int)((fr.w >> 12) & 0xFFF), (int)((fr.z >> 24) | (((fr.w >> 24) & 0xFu) << 8))};

@@ -69,33 +69,27 @@ __device__ __forceinline__ uint32_t eval_uniform(int K, uint4 rec, int k, const 
 }
 
 // Functions with more than 5 inputs ("wide"): a multiplexer tree would have
-// 2^k leaves, so the warp looks the value up chain by chain instead.  For
-// every lane that asks (`mine`), in turn: its record and chain group are
-// broadcast, lane q gathers chain q's table index from the k parents' state
-// words (bit q of each) and reads that bit of the table, and one ballot
-// collects the 32 chains' values for the asking lane.  All 32 lanes must call.
-static __device__ __noinline__ uint32_t eval_wide_warp(bool mine, uint4 rec, const uint32_t *cur, int gpb, int gl,
-                                                   const uint32_t *wide_tt, const uint16_t *wide_par) {
-  const int lane = threadIdx.x & 31;
-  uint32_t result = 0u;
-  unsigned pend = __ballot_sync(kFull, mine);
-  while (pend) {
-    const int src = __ffs(pend) - 1;
-    pend &= pend - 1;
-    const uint32_t tt0 = __shfl_sync(kFull, rec.x, src);
-    const uint32_t p0 = __shfl_sync(kFull, rec.z, src);
-    const int k = (int)(__shfl_sync(kFull, rec.w, src) >> 28);
-    const int g = __shfl_sync(kFull, gl, src);
+// 2^k leaves, so the thread looks the value up chain by chain instead, and
+// only for the chains that selected the function (`lanes`): chain q's table
+// index gathers bit q of the k parents' state words, and bit q of the result
+// is that entry of the table.  Over an item's functions every chain is looked
+// up once.
+static __device__ __noinline__ uint32_t eval_wide_lanes(uint4 rec, uint32_t lanes, const uint32_t *cur, int gpb,
+                                                        int gl, const uint32_t *wide_tt, const uint16_t *wide_par) {
+  const int k = fn_k(rec);
+  uint32_t w[PBN_MAX_PARENTS];
+#pragma unroll
+  for (int m = 0; m < PBN_MAX_PARENTS; m++) w[m] = m < k ? cur[(int)wide_par[rec.z + m] * gpb + gl] : 0u;
+  uint32_t out = 0u;
+  while (lanes) {
+    const int q = __ffs(lanes) - 1;
+    lanes &= lanes - 1;
     uint32_t idx = 0u;
-    for (int m = 0; m < k; m++) {
-      const uint32_t w = cur[(int)wide_par[p0 + m] * gpb + g];  // one address for the whole warp
-      idx |= ((w >> lane) & 1u) << m;
-    }
-    const uint32_t bit = (wide_tt[tt0 + (idx >> 5)] >> (idx & 31u)) & 1u;
-    const uint32_t v = __ballot_sync(kFull, bit != 0u);
-    if (lane == src) result = v;
+#pragma unroll
+    for (int m = 0; m < PBN_MAX_PARENTS; m++) idx |= ((w[m] >> q) & 1u) << m;
+    out |= ((wide_tt[rec.x + (idx >> 5)] >> (idx & 31u)) & 1u) << q;
   }
-  return result;
+  return out;
 }
 
 struct ItemCtx {
@@ -222,7 +216,7 @@ __device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, con
       const int kt = wide ? 0 : k;
       const int K = __reduce_max_sync(kFull, (unsigned)kt);
       if (__any_sync(kFull, has && !wide)) fword |= (wide ? 0u : my_sel) & eval_uniform(K, tr, kt, c.cur, c.gpb, c.gl);
-      fword |= my_sel & eval_wide_warp(wide, rec, c.cur, c.gpb, c.gl, c.wide_tt, c.wide_par);
+      if (wide) fword |= eval_wide_lanes(rec, my_sel, c.cur, c.gpb, c.gl, c.wide_tt, c.wide_par);
     } else {
       const int K = __reduce_max_sync(kFull, (unsigned)k);
       if (__any_sync(kFull, has)) fword |= my_sel & eval_uniform(K, rec, k, c.cur, c.gpb, c.gl);

@@ -200,6 +200,25 @@ def wide_config(seed: int = BASE_SEED + 5, n: int = 4096) -> tuple:
     return net, np.arange(10, dtype=np.int32), dict(omega=16384, rhat=1.05, rel=0.01, alpha=0.05)
 
 
+# Density classes of the paper's sweep (Sec. 5.1): the density D(G) is the
+# parent count of all functions over n, about (functions per node) x (parents
+# per function).  Sparse ~10 and in-between 50-100 are drawn here; dense
+# (150-300) needs more functions or inputs than this build takes (8 functions
+# of at most 12 inputs give at most 96).
+DENSITY_CLASSES = {"sparse": ((2, 4), (2, 5)), "in-between": ((6, 8), (7, 12))}
+
+
+def sweep_config(n: int, density: str, seed: int = BASE_SEED + 7) -> tuple:
+    """One model of the paper-shaped sweep: n nodes, the density class's
+    function and parent ranges, biased truth tables, p = 0.001; state of
+    interest: 3 random nodes with random values."""
+    fns, pars = DENSITY_CLASSES[density]
+    s = seed + 1000 * n + (0 if density == "sparse" else 1)
+    net = random_pbn(s, n, fns, pars, "biased", "uniform", 0.001, f"sweep-{density}-n{n}")
+    soi = random_soi(np.random.default_rng(s), n, 3, 3)
+    return net, soi
+
+
 def _log_uniform_int(rng, lo, hi):
     return int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
 
