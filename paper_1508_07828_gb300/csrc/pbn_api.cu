@@ -296,21 +296,22 @@ int plan_select(const pbn::NetDev &net, int64_t omega, int gpb_req, int threads_
       return fail(PBN_ERR_UNSUPPORTED, "select-ahead shared memory does not fit (n %d, F %d)", net.n, net.F);
     gpb = std::max(1, gpb / 2);
   }
-  // Threads per item unless asked: 2 while the items of a CTA are few enough
-  // for the register-resident path (the step is a chain of dependent
-  // operations, so spreading it over more warps pays), 1 beyond (there extra
-  // threads only multiply the work of the generic path).  Measured on GB300
-  // over n = 100 .. 3000 with 256 .. 4096 chains.
-  const int T = T_req > 0 ? T_req : (net.n * gpb <= 300 && !net.has_wide ? 2 : 1);
+  // Threads per item unless asked (measured on GB300 over n = 100 .. 3000 with
+  // 256 .. 4096 chains): 1 when every function of an item stays in registers
+  // (at most two per node) or when the CTA holds more than 240 items (two
+  // threads per item would no longer fit the register-resident path); else 2,
+  // which splits the per-step decoding of a node's further functions.
+  const bool two = net.max_l > 2 && net.n * gpb <= 240 && !net.has_wide;
+  const int T = T_req > 0 ? T_req : (two ? 2 : 1);
   if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
   if (net.has_wide && T != 1)
     return fail(PBN_ERR_UNSUPPORTED, "functions with more than 5 inputs run one thread per item");
   const int items = net.n * gpb;
   const int tmax = pbn::apply_threads_limit(T);
-  // with T > 1 and one item per T threads, one more warp feeds the others
+  // with one item per T threads for the whole launch, one more warp feeds the others
   const int item_threads = (items * T + 31) / 32 * 32;
   int threads = threads_req > 0                                  ? threads_req
-                : (T > 1 && item_threads + 32 <= tmax)           ? item_threads + 32
+                : (!net.has_wide && item_threads + 32 <= tmax)    ? item_threads + 32
                                                                  : std::min(tmax, std::max(32, item_threads));
   if (threads % 32 || threads > tmax || threads < 32)
     return fail(PBN_ERR_INVALID, "threads_per_block %d (a multiple of 32, at most %d here)", threads, tmax);

@@ -216,12 +216,13 @@ struct ResidentItem {
   }
 };
 
-// Threads per CTA an apply variant is compiled for: T = 2 keeps twice the
-// leaves of T = 4 in registers, so it gets 128 registers per thread.
+// Threads per CTA an apply variant is compiled for: with one or two threads
+// per item a thread keeps 32 or 16 leaves per function in registers, so those
+// variants get 128 registers per thread (512 threads); four threads, 64.
 template <int T>
-constexpr int apply_max_threads() { return T == 2 ? 512 : 1024; }
+constexpr int apply_max_threads() { return T == 4 ? 1024 : 512; }
 
-int apply_threads_limit(int T) { return T == 2 ? apply_max_threads<2>() : apply_max_threads<4>(); }
+int apply_threads_limit(int T) { return T == 4 ? apply_max_threads<4>() : apply_max_threads<1>(); }
 
 // One CTA per `gpb` chain groups applies a.steps steps of category words;
 // T threads per (node, group) item.
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
     nxt[idx] = v;
     return v;
   };
-  if (!WIDE && T > 1 && items * T <= (int)blockDim.x - 32) {
+  if (!WIDE && items * T <= (int)blockDim.x - 32) {
     // One item per T threads for the whole launch, everything that does not
     // change from step to step in registers; the last warp is the producer:
     // it waits for the category words, writes the indicator and requests the
