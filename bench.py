@@ -356,7 +356,7 @@ def run_ours(args):
     groups_steps = items / net.n
     peak, sms, mhz, peak_src = alu_peak_tops(local)
     if apply_launches:
-        kernel, k_ms, k_launches = "apply_kernel", apply_ms, apply_launches
+        kernel, k_ms, k_launches = "apply_resident_kernel", apply_ms, apply_launches
         ops_per_group_step = float(apply_ops_per_item(net).sum())
         other = {"select_kernel": {"achieved": float(draw_ops_per_item(net).sum()) * groups_steps /
                                    ((sim_ms - apply_ms) / 1e3) / 1e12, "ms": sim_ms - apply_ms,

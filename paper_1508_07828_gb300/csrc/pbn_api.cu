@@ -224,14 +224,18 @@ int check_props(const pbn_run_cfg &cfg, int n) {
 
 int n_recorded_props(const pbn_run_cfg &cfg) { return cfg.n_props > 0 ? cfg.n_props : (cfg.soi.size > 0 ? 1 : 0); }
 
-// Select-ahead scratch per (device, stream): the category words of one chunk
-// and, for global perturbation, their per-group OR.  Grown on the stream, so
-// launches already queued keep the old buffer until they finish.
+// Select-ahead scratch per (device, stream): the category words of a chunk
+// of steps (for global perturbation with their per-group OR in word F of each
+// run), two buffers when chunks are pipelined.  Grown on the stream, so
+// launches already queued keep the old buffer until they finish.  A
+// pipelined run draws chunk i+1 on the side stream while chunk i is applied
+// on the caller's stream; events order the two (start; selected[b],
+// applied[b] per buffer).
 struct SelectScratch {
-  uint32_t *planes = nullptr;
-  size_t planes_words = 0;
-  uint32_t *anyw = nullptr;
-  size_t any_words = 0;
+  uint32_t *planes[2] = {nullptr, nullptr};
+  size_t planes_words[2] = {0, 0};
+  cudaStream_t side = nullptr;
+  cudaEvent_t start = nullptr, selected[2] = {nullptr, nullptr}, applied[2] = {nullptr, nullptr};
 };
 std::mutex g_sel_mu;
 std::map<std::pair<int, cudaStream_t>, SelectScratch> g_sel;
@@ -252,27 +256,44 @@ int grow(uint32_t *&buf, size_t &have, size_t words, cudaStream_t s) {
 }
 
 // Largest chunk of the select-ahead schedule: 1024 steps, or fewer when the
-// category words of all groups would exceed 64 MiB (they stay in L2 between
-// the two kernels at the chain counts this schedule is for).
+// category words of all groups would exceed 32 MiB per buffer (both buffers
+// of a pipelined run stay in L2 between the kernels at the chain counts this
+// schedule is for).  A run longer than one chunk starts with kSelectFirst
+// steps and doubles the chunk up to the largest, so the first apply starts
+// early and every later chunk is drawn while the previous one is applied.
 constexpr int64_t kSelectMaxSteps = 1024;
-constexpr int64_t kSelectBudgetBytes = 64ll << 20;
+constexpr int64_t kSelectBudgetBytes = 32ll << 20;
+constexpr int64_t kSelectFirst = 128;
+
+int ensure_side(SelectScratch *sc) {
+  if (sc->side) return PBN_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&sc->side, cudaStreamNonBlocking);
+  cudaEvent_t *evs[5] = {&sc->start, &sc->selected[0], &sc->selected[1], &sc->applied[0], &sc->applied[1]};
+  for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(evs[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PBN_ERR_CUDA, "select-ahead side stream: %s", cudaGetErrorString(e));
+  }
+  return PBN_OK;
+}
 
 struct SelectPlan {
   int gpb, threads, staging, W, ring, T;
+  bool resident;  // apply_resident_kernel (one thread per item, `ring` slots of bulk copies)
   size_t smem;
 };
 
 // Launch shape of the select-ahead schedule, or PBN_ERR_UNSUPPORTED when its
 // shared memory does not fit (staging_req: public values 0, 1, 3; 2 = tiles
 // is not supported).
-int plan_select(const pbn::NetDev &net, int64_t omega, int gpb_req, int threads_req, int T_req, int staging_req,
-                int n_props, SelectPlan *p) {
+int plan_select(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, int threads_req, int T_req,
+                int staging_req, int n_props, SelectPlan *p) {
   const int G = (int)((omega + 31) / 32);
   const int maxs = pbn::sim_max_smem();
   if (staging_req == 2) return fail(PBN_ERR_UNSUPPORTED, "select-ahead schedule with TMA tiles");
   int gpb = gpb_req > 0 ? gpb_req : std::max(1, (G + sm_count() - 1) / sm_count());
   gpb = std::min(gpb, std::max(G, 1));
-  const int W = (net.F + 3) & ~3;
+  const int W = (net.F + (mode == PBN_PERTURB_GLOBAL ? 1 : 0) + 3) & ~3;
   // a deep ring (latency of the category words hidden 7 steps ahead) before
   // tables in shared memory; the records a warp reads stay in L1 otherwise
   const int opts[4][2] = {{8, pbn::STAGE_SMEM}, {8, pbn::STAGE_GLOBAL}, {3, pbn::STAGE_SMEM}, {3, pbn::STAGE_GLOBAL}};
@@ -319,6 +340,27 @@ int plan_select(const pbn::NetDev &net, int64_t omega, int gpb_req, int threads_
   p->gpb = gpb;
   p->threads = threads;
   p->W = W;
+  p->resident = false;
+  // One thread per item asked for, every item resident for the whole launch:
+  // the register-resident kernel (two threads per item, one per function
+  // slot) with a ring of bulk-copied steps, 16 slots or fewer when shared
+  // memory is short; staging requests other than tiles read the records
+  // beyond a node's second from global memory there.
+  const int pair_threads = (2 * items + 31) / 32 * 32;
+  if (T == 1 && !net.has_wide && items <= pbn::kResidentItems &&
+      (threads_req == 0 || threads_req == pair_threads + 32)) {
+    for (int lg = 4; lg >= 2; lg--) {
+      const size_t b = pbn::apply_resident_smem_bytes(gpb, W, 1 << lg, n_props);
+      if ((int64_t)b <= maxs) {
+        p->resident = true;
+        p->ring = lg;
+        p->staging = pbn::STAGE_GLOBAL;
+        p->smem = b;
+        p->threads = pair_threads + 32;
+        break;
+      }
+    }
+  }
   return PBN_OK;
 }
 
@@ -335,7 +377,7 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
   const int G = (int)((ch.omega + 31) / 32);
   const int64_t per_step = (int64_t)G * sp.W * 4;
   const int64_t C = std::max<int64_t>(1, std::min(kSelectMaxSteps, kSelectBudgetBytes / per_step));
-  const int64_t first = std::min(C, steps);
+  const bool pipe = steps > C;
   SelectScratch *sc;
   {
     int dev = 0;
@@ -343,27 +385,62 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
     std::lock_guard<std::mutex> lk(g_sel_mu);
     sc = &g_sel[std::make_pair(dev, s)];
   }
-  int rc = grow(sc->planes, sc->planes_words, (size_t)first * G * sp.W, s);
+  const size_t words = (size_t)std::min(C, steps) * G * sp.W;
+  int rc = grow(sc->planes[0], sc->planes_words[0], words, s);
   if (rc) return rc;
-  if (cfg.perturb_mode == PBN_PERTURB_GLOBAL && (rc = grow(sc->anyw, sc->any_words, (size_t)first * G, s)))
-    return rc;
+  if (pipe) {
+    if ((rc = grow(sc->planes[1], sc->planes_words[1], words, s)) || (rc = ensure_side(sc))) return rc;
+    // the side stream starts after everything queued on the caller's stream
+    CUDA_TRY(cudaEventRecord(sc->start, s), "event");
+    CUDA_TRY(cudaStreamWaitEvent(sc->side, sc->start, 0), "stream wait");
+  }
+  // While chunk i is applied, chunk i+1 is drawn on the SMs the apply CTAs
+  // leave free: an apply CTA and a select block together ask for more shared
+  // memory than an SM has, so select blocks (four per SM) never share an SM
+  // with the latency-bound apply, which keeps its issue slots.
+  size_t select_pad = 0, apply_smem = sp.smem;
+  if (pipe && (G + sp.gpb - 1) / sp.gpb < sm_count()) {
+    int dev = 0, per_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) {
+      const int64_t pad = per_sm / 4 - reserved;
+      const int64_t need = (int64_t)per_sm - pad - 2 * reserved + 16;
+      if (pad > 0 && need <= pbn::sim_max_smem()) {
+        select_pad = (size_t)pad;
+        apply_smem = std::max(apply_smem, (size_t)need);
+      }
+    } else {
+      cudaGetLastError();
+    }
+  }
   LaunchPlan lp;
   lp.gpb = sp.gpb;
   lp.threads = sp.threads;
   lp.T = 1;
   lp.BPR = 1;
-  lp.smem = sp.smem;
+  lp.smem = apply_smem;
   lp.staging = sp.staging;
-  for (int64_t done = 0; done < steps; done += C) {
-    const int64_t k = std::min(C, steps - done);
+  int64_t k = 0;
+  for (int64_t done = 0, i = 0; done < steps; done += k, i++) {
+    k = pipe ? std::min(std::min(C, kSelectFirst << std::min<int64_t>(i, 20)), steps - done) : steps - done;
+    const int b = pipe ? (int)(i & 1) : 0;
+    cudaStream_t ss = pipe ? sc->side : s;
     pbn::SimArgs a = make_args(net, cfg, ch, k, lp);
     if (!record) a.soi_size = 0;
     a.W = sp.W;
-    a.planes = sc->planes;
-    a.anyw = sc->anyw;
-    if (cfg.perturb_mode == PBN_PERTURB_GLOBAL)
-      CUDA_TRY(cudaMemsetAsync(sc->anyw, 0, (size_t)k * G * 4, s), "select-ahead clear");
-    CUDA_TRY(pbn::launch_select(a, cfg.perturb_mode, 1, s), "select launch");
+    a.planes = sc->planes[b];
+    a.ring_log2 = sp.resident ? sp.ring : 0;
+    // buffer b was last read by the apply of chunk i-2
+    if (pipe && i >= 2) CUDA_TRY(cudaStreamWaitEvent(ss, sc->applied[b], 0), "stream wait");
+    if (cfg.perturb_mode == PBN_PERTURB_GLOBAL)  // word F of every (step, group) run: OR-ed into by select
+      CUDA_TRY(cudaMemset2DAsync(a.planes + net.F, (size_t)sp.W * 4, 0, 4, (size_t)k * G, ss),
+               "select-ahead clear");
+    CUDA_TRY(pbn::launch_select(a, cfg.perturb_mode, 1, ss, select_pad), "select launch");
+    if (pipe) {
+      CUDA_TRY(cudaEventRecord(sc->selected[b], ss), "event");
+      CUDA_TRY(cudaStreamWaitEvent(s, sc->selected[b], 0), "stream wait");
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timing) {
       e0 = timing->next(timing->ctx);
@@ -371,11 +448,16 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
       if (!e0 || !e1) return fail(PBN_ERR_CUDA, "event creation failed");
       CUDA_TRY(cudaEventRecord(e0, s), "event");
     }
-    CUDA_TRY(pbn::launch_apply(a, cfg.perturb_mode, sp.ring, sp.T, sp.threads, sp.smem, s), "apply launch");
+    if (sp.resident)
+      CUDA_TRY(pbn::launch_apply_resident(a, cfg.perturb_mode, net.max_l > 2, sp.threads, apply_smem, s),
+               "apply launch");
+    else
+      CUDA_TRY(pbn::launch_apply(a, cfg.perturb_mode, sp.ring, sp.T, sp.threads, apply_smem, s), "apply launch");
     if (timing) {
       CUDA_TRY(cudaEventRecord(e1, s), "event");
       timing->pairs.emplace_back(e0, e1);
     }
+    if (pipe) CUDA_TRY(cudaEventRecord(sc->applied[b], s), "event");
     ch.length += k;
     if (launches) *launches += 2;
   }
@@ -408,8 +490,8 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
   if (want_select) {
     SelectPlan sp;
     const std::string saved = g_err;
-    int rc = plan_select(net, ch.omega, cfg.groups_per_block, cfg.threads_per_block, cfg.threads_per_item,
-                         cfg.staging, n_recorded_props(cfg), &sp);
+    int rc = plan_select(net, ch.omega, cfg.perturb_mode, cfg.groups_per_block, cfg.threads_per_block,
+                         cfg.threads_per_item, cfg.staging, n_recorded_props(cfg), &sp);
     if (rc == PBN_OK) return run_select_ahead(net, cfg, ch, steps, record, sp, s, launches, timing);
     if (cfg.schedule == PBN_SCHEDULE_SELECT_AHEAD) return rc;
     g_err = saved;  // automatic choice: fall back to the fused schedule

@@ -109,9 +109,10 @@ struct SimArgs {
   const uint32_t *wide_tt;   // tables and parents of functions with more than 5 inputs (NetDev)
   const uint16_t *wide_par;
   int has_wide;
-  int W;                 // select-ahead: category words per (step, group), F rounded up to 4
+  int W;                 // select-ahead: category words per (step, group): F (+1 under global
+                         // perturbation: word F is the OR of the perturbed lanes), rounded up to 4
   uint32_t *planes;      // select-ahead: category words [steps][G][W] of the chunk
-  uint32_t *anyw;        // select-ahead, global perturbation: [steps][G] OR of the perturbed lanes
+  int ring_log2;         // select-ahead, register-resident apply: log2 of the ring slots
   int n_props;           // properties recorded (entries soi_node[m] belong to property soi_prop[m])
   int64_t prop_stride;   // words between two properties' bitstreams (G * bits_cap)
   uint8_t soi_prop[kMaxSoi];
@@ -129,10 +130,19 @@ cudaError_t launch_sim(const SimArgs &a, int mode, int T, int BPR, int threads, 
 size_t sim_smem_bytes(int n, int F, int gpb, int mode, int staging, int tile_bytes);
 // Select-ahead schedule (pbn_split.cu): the category words of a.steps steps
 // of all groups, then their application (a.staging: STAGE_SMEM or STAGE_GLOBAL).
-cudaError_t launch_select(const SimArgs &a, int mode, int BPR, cudaStream_t s);
+// pad: unused dynamic shared memory per block (placement only; 0 = none).
+cudaError_t launch_select(const SimArgs &a, int mode, int BPR, cudaStream_t s, size_t pad = 0);
 // T = threads per (node, group) item: 1, 2 or 4 (each a share of the depth-5 tree).
 cudaError_t launch_apply(const SimArgs &a, int mode, int ring, int T, int threads, size_t smem, cudaStream_t s);
 size_t apply_smem_bytes(int n, int F, int gpb, int W, int staging, int ring, int n_props);
+// Register-resident apply (two threads per item, at most kResidentItems items
+// per CTA, no function with more than 5 inputs; function records beyond a
+// node's second are read from global memory): threads = 2 x items rounded up
+// to a warp, plus one producer warp; ring = 4, 8 or 16 slots.
+constexpr int kResidentItems = 480;
+// rest: some node has more than two functions (compiles that path in).
+cudaError_t launch_apply_resident(const SimArgs &a, int mode, bool rest, int threads, size_t smem, cudaStream_t s);
+size_t apply_resident_smem_bytes(int gpb, int W, int ring, int n_props);
 int apply_threads_limit(int T);  // largest CTA of the apply variant for T
 // Device status word of the simulation kernels on the current device (0 = ok).
 int *device_status();

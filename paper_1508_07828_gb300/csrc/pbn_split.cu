@@ -20,11 +20,14 @@
 //   w = 1 .. l-1:   lanes that selected function w-1
 // The last function's lanes are the valid lanes in none of those words.
 // Global perturbation also stores, per (s, g), the OR of all nodes' w = 0
-// words (anyw[s * G + g]): the chains that take s XOR gamma.
+// words in word F of the same run (W = F + 1 rounded up to 4): the chains
+// that take s XOR gamma.  A step's words of consecutive groups are one
+// contiguous, 16-byte aligned run, so one bulk copy moves a CTA's step.
 //
 // Both kernels compare the same digits against the same bounds as the fused
 // kernel (draw_below), so the chains are bit-identical under either schedule.
 #include <algorithm>
+#include <type_traits>
 
 #include "pbn_step.cuh"
 
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Sim
   c.t = a.t0 + (uint64_t)s;
   c.sub = 0;
   uint32_t *out = a.planes + sg * a.W + c.f0;
-  uint32_t *anyw = a.anyw + sg;
+  uint32_t *anyw = a.planes + sg * a.W + a.F;
   switch ((int)__reduce_max_sync(kFull, (unsigned)c.L)) {
     case 0: break;
     case 1: select_item<1, MODE, BPR>(a.rk, a.P32, c, out, anyw); break;
@@ -93,11 +96,6 @@ namespace {
 
 __device__ __forceinline__ void copy16_async(void *dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-
-__device__ __forceinline__ void copy4_async(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(__cvta_generic_to_global(src))
                : "memory");
 }
 
@@ -118,8 +116,7 @@ constexpr int kIndRing = 64;
 // Ring slots of category words: RING - 1 steps are in flight ahead of the
 // step being applied (8, or 3 when 8 slots do not fit shared memory).
 size_t apply_smem_bytes(int n, int F, int gpb, int W, int staging, int ring, int n_props) {
-  size_t b = (size_t)ring * gpb * W * 4;                      // category words ring
-  b += (size_t)ring * (((size_t)gpb + 3) & ~(size_t)3) * 4;   // OR-of-perturbations ring
+  size_t b = (size_t)ring * gpb * W * 4;  // category words ring
   if (staging == STAGE_SMEM) b += (size_t)F * 16;
   b += ((size_t)n * 4 + 15) & ~(size_t)15;                 // node records
   b += 2 * (size_t)n * gpb * 4;                            // current and next state
@@ -232,10 +229,8 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
   const int gpb = a.gpb, n = a.n, W = a.W;
   const uint32_t g0 = blockIdx.x * (uint32_t)gpb;
   const int ngl = min(gpb, a.G - (int)g0);
-  const int gpbA = (gpb + 3) & ~3;
   uint32_t *ring = reinterpret_cast<uint32_t *>(smem);
-  uint32_t *ring_any = ring + (size_t)kRing * gpb * W;
-  unsigned char *p = reinterpret_cast<unsigned char *>(ring_any + (size_t)kRing * gpbA);
+  unsigned char *p = reinterpret_cast<unsigned char *>(ring + (size_t)kRing * gpb * W);
   const uint4 *fn_s = a.fn;
   const bool tt_replicated = a.staging == STAGE_SMEM;
   if (tt_replicated) {
@@ -270,9 +265,6 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
       const uint32_t *src = a.planes + ((size_t)s * a.G + g0) * W;
       uint32_t *dst = ring + (size_t)(s % kRing) * gpb * W;
       for (int j = threadIdx.x; j < chunks16; j += blockDim.x) copy16_async(dst + 4 * j, src + 4 * j);
-      if (MODE == PBN_PERTURB_GLOBAL)
-        for (int gl = threadIdx.x; gl < ngl; gl += blockDim.x)
-          copy4_async(ring_any + (s % kRing) * gpbA + gl, a.anyw + (size_t)s * a.G + g0 + gl);
     }
     async_commit();  // one group per step, empty past the end, so the wait count stays uniform
   };
@@ -339,20 +331,23 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
       }
     }
   };
-  auto finish = [&](int idx, int gl, uint32_t P, uint32_t fword, const uint32_t *slot_any) -> uint32_t {
+  // slot: the step's words of this CTA's groups (word F of a group's run is
+  // the OR of its perturbed lanes under global perturbation)
+  auto finish = [&](int idx, int gl, uint32_t P, uint32_t fword, const uint32_t *slot) -> uint32_t {
     uint32_t v;
     if (MODE == PBN_PERTURB_PER_NODE) {
       v = (P & ~cur[idx]) | fword;
     } else {
-      const uint32_t any = slot_any[gl];
+      const uint32_t any = slot[gl * W + a.F];
       v = (any & (cur[idx] ^ P)) | (~any & fword);
     }
     nxt[idx] = v;
     return v;
   };
-  if (!WIDE && items * T <= (int)blockDim.x - 32) {
-    // One item per T threads for the whole launch, everything that does not
-    // change from step to step in registers; the last warp is the producer:
+  if (T > 1 && !WIDE && items * T <= (int)blockDim.x - 32) {
+    // One item per T (2 or 4) threads for the whole launch (one thread per
+    // item runs in apply_resident_kernel), everything that does not change
+    // from step to step in registers; the last warp is the producer:
     // it waits for the category words, writes the indicator and requests the
     // words of later steps, so the item warps only compute between barriers.
     const bool producer = warp == nwarps - 1;
@@ -378,9 +373,6 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
         const uint32_t *src = a.planes + ((size_t)s * a.G + g0) * W;
         uint32_t *dst = ring + (size_t)(s % kRing) * slot_words;
         for (int j = lane; j < chunks16; j += 32) copy16_async(dst + 4 * j, src + 4 * j);
-        if (MODE == PBN_PERTURB_GLOBAL)
-          for (int g = lane; g < ngl; g += 32)
-            copy4_async(ring_any + (s % kRing) * gpbA + g, a.anyw + (size_t)s * a.G + g0 + g);
       }
       async_commit();
     };
@@ -436,7 +428,7 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
           if (LW > kResident) eval_rest(kResident, LW, L, f0, gl, sub, w, rest, fword);
         }
         if (active && sub == 0) {
-          const uint32_t v = finish(idx, gl, P, fword, ring_any + ring_slot * gpbA);
+          const uint32_t v = finish(idx, gl, P, fword, ring + ring_slot * slot_words);
           for (uint32_t props = in_props; props; props &= props - 1) {
             const int m = __ffs(props) - 1;
             const uint32_t term = ((need1 >> m) & 1u ? v : kFull) & ((need0 >> m) & 1u ? ~v : kFull);
@@ -474,7 +466,7 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
         const int LW = (int)__reduce_max_sync(kFull, (unsigned)L);
         uint32_t fword = 0u;
         eval_rest(0, LW, L, f0, gl, sub, w, rest, fword);
-        if (active && sub == 0) finish(node_id(rec) * gpb + gl, gl, P, fword, ring_any + (s % kRing) * gpbA);
+        if (active && sub == 0) finish(node_id(rec) * gpb + gl, gl, P, fword, slot);
       }
       uint32_t *tmp = cur;
       cur = nxt;
@@ -490,23 +482,422 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident apply: two threads per (node, group) item, one per
+// function slot.
+//
+// Thread 2i+f holds function f (f = 0, 1) of item i, decoded once per launch:
+// its truth table as leaf pairs in registers (leaf 2q as 0 / ~0 and its XOR
+// with leaf 2q+1) and the shared-memory addresses of its parents' state
+// words.  A step then reads five parent words and runs one depth-5
+// multiplexer tree (tables are replicated to 32 leaves, so inputs k..4 select
+// between equal halves); each thread masks its value with the lanes that
+// selected its function(s) and one shuffle ORs the pair.  Every tree has
+// depth 5: warps of equal work keep the per-step barrier short (measured on
+// GB300: a loop per warp-uniform depth runs fewer instructions but the
+// deepest warps then set every step, and the step got longer).  Functions j >= 2
+// (nodes with more than two) are decoded from their records every step,
+// thread f taking those with j = f mod 2.  Two threads per item give every
+// scheduler two or more warps of equal work, so the dependent levels of one
+// warp's trees overlap with another's.
+//
+// Feeding: the category words of one step for the CTA's groups are one
+// contiguous run, so one thread of the last warp (the producer) moves a step
+// with one bulk copy (cp.async.bulk) into a ring slot, completing the slot's
+// mbarrier.  Between the barriers of steps s-1 and s it refills the slot that
+// step s-1 used and waits for the words of step s+1, so the barrier that ends
+// step s also publishes them; the item threads never wait on an mbarrier.
+// The wait is bounded (1 s): if it gives up, the producer records
+// PBN_ERR_TIMEOUT in the device status word, issues nothing more and lets the
+// launch run to its end (the results are then invalid and the status says
+// so); before the CTA leaves it waits (bounded) for every copy it issued.
+//
+// The two state buffers sit at fixed shared offsets (kResStride words apart)
+// so a step's loads and store are register + immediate addresses, with the
+// step loop unrolled by two.
+
+namespace {
+
+constexpr int kResStride = 512;  // words between the two state buffers
+
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+template <int OFF>
+__device__ __forceinline__ uint32_t lds_u32_at(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1 + %2];" : "=r"(v) : "r"(addr), "n"(OFF));
+  return v;
+}
+
+template <int OFF>
+__device__ __forceinline__ void sts_u32_at(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0 + %1], %2;" ::"r"(addr), "n"(OFF), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void atom_and_shared(uint32_t addr, uint32_t v) {
+  asm volatile("atom.shared.and.b32 _, [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// CTA-wide barrier in its non-aligned form: the producer warp and the item
+// warps reach it from different loops.
+__device__ __forceinline__ void cta_barrier() { asm volatile("barrier.sync 0;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for a phase of an mbarrier for at most kWaitLimitNs.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_try(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity) {
+  return mbar_try(bar, parity) || mbar_wait_slow(bar, parity);
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// One function of an item, decoded once per launch.
+struct ResidentFn {
+  uint32_t lo[16], dx[16];
+  uint32_t par[5];  // shared addresses of the parents' words in state buffer 0
+
+  __device__ __forceinline__ void load(uint4 fr, uint32_t st0, int gpb, int gl) {
+    const uint32_t tt5 = replicate5(fr.x, fn_k(fr));
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+      lo[q] = sext_bit(tt5, 2 * q);
+      dx[q] = lo[q] ^ sext_bit(tt5, 2 * q + 1);
+    }
+    const int pr[5] = {(int)(fr.z & 0xFFF), (int)((fr.z >> 12) & 0xFFF), (int)(fr.w & 0xFFF),
+                       (int)((fr.w >> 12) & 0xFFF), (int)((fr.z >> 24) | (((fr.w >> 24) & 0xFu) << 8))};
+#pragma unroll
+    for (int m = 0; m < 5; m++) par[m] = st0 + 4u * (uint32_t)(pr[m] * gpb + gl);
+  }
+
+  __device__ __forceinline__ void clear(uint32_t st0) {
+#pragma unroll
+    for (int q = 0; q < 16; q++) lo[q] = dx[q] = 0u;
+#pragma unroll
+    for (int m = 0; m < 5; m++) par[m] = st0;
+  }
+
+  // subtree of level M over leaf pairs [Q, Q + 2^(M-1)), depth first so few
+  // partial results are live at once
+  template <int M, int Q>
+  __device__ __forceinline__ uint32_t sub(const uint32_t (&x)[5]) const {
+    if constexpr (M == 1) {
+      return lo[Q] ^ (x[0] & dx[Q]);
+    } else {
+      const uint32_t a = sub<M - 1, Q>(x), b = sub<M - 1, Q + (1 << (M - 2))>(x);
+      return (x[M - 1] & b) | (~x[M - 1] & a);
+    }
+  }
+
+  // the function on state buffer OFF (byte offset of the buffer)
+  template <int OFF>
+  __device__ __forceinline__ uint32_t eval() const {
+    uint32_t x[5];
+#pragma unroll
+    for (int m = 0; m < 5; m++) x[m] = lds_u32_at<OFF>(par[m]);
+    return sub<5, 0>(x);
+  }
+};
+
+// Depth-first multiplexer tree of a truth table replicated to 32 leaves:
+// subtree of level M over leaves [Q, Q + 2^M).
+template <int M, int Q>
+__device__ __forceinline__ uint32_t tt_subtree(uint32_t tt5, const uint32_t (&x)[5]) {
+  if constexpr (M == 0) {
+    return sext_bit(tt5, Q);
+  } else {
+    const uint32_t a = tt_subtree<M - 1, Q>(tt5, x), b = tt_subtree<M - 1, Q + (1 << (M - 1))>(tt5, x);
+    return (x[M - 1] & b) | (~x[M - 1] & a);
+  }
+}
+
+// An item of a node with more than two functions (LW > 2, warp-uniform):
+// this thread's functions j = f, f+2, ... < LW, the resident one (value v)
+// first, further ones decoded from their records; the lanes of function
+// j < L-1 are category word 1+j, the last function's are the lanes in none of
+// them.
+__device__ __forceinline__ uint32_t rest_part(uint32_t w, int L, int LW, int f, uint32_t rest, uint32_t v,
+                                              uint32_t cur, const uint4 *fn, int f0, int gpb, int gl) {
+  uint32_t taken = 0u;
+  for (int j = 0; j + 1 < L; j++) taken |= lds_u32(w + 4u * (uint32_t)(1 + j));
+  auto lanes_of = [&](int j) -> uint32_t {
+    if (j + 1 < L) return lds_u32(w + 4u * (uint32_t)(1 + j));
+    return j + 1 == L ? rest & ~taken : 0u;
+  };
+  uint32_t part = lanes_of(f) & v;
+  // the same trip count in every lane (the warp votes in each round)
+#pragma unroll 1
+  for (int jb = 2; jb < LW; jb += 2) {
+    const int j = jb + f;
+    const uint32_t sel = j < L ? lanes_of(j) : 0u;
+    const bool has = sel != 0u;
+    if (__any_sync(kFull, has)) {
+      const uint4 fr = has ? fn[f0 + j] : make_uint4(0u, 0u, 0u, 0u);
+      const int pr[5] = {(int)(fr.z & 0xFFF), (int)((fr.z >> 12) & 0xFFF), (int)(fr.w & 0xFFF),
+                         (int)((fr.w >> 12) & 0xFFF), (int)((fr.z >> 24) | (((fr.w >> 24) & 0xFu) << 8))};
+      uint32_t x[5];
+#pragma unroll
+      for (int m = 0; m < 5; m++) x[m] = lds_u32(cur + 4u * (uint32_t)(pr[m] * gpb + gl));
+      part |= sel & tt_subtree<5, 0>(replicate5(fr.x, fn_k(fr)), x);
+    }
+  }
+  return part;
+}
+
+}  // namespace
+
+size_t apply_resident_smem_bytes(int gpb, int W, int ring, int n_props) {
+  size_t b = (size_t)2 * kResStride * 4;                     // state buffers
+  b += (size_t)ring * gpb * W * 4;                           // category words ring (16-byte slots)
+  b += (size_t)ring * 8;                                     // one mbarrier per slot
+  b += (size_t)std::max(n_props, 1) * gpb * kIndRing * 4;    // indicator words of recent steps
+  return b;
+}
+
+// REST: compiled with the path of nodes with more than two functions (a
+// network whose nodes have at most two runs the variant without it).
+template <int MODE, bool REST>
+__global__ void __launch_bounds__(2 * kResidentItems + 32, 1) apply_resident_kernel(const __grid_constant__ SimArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int gpb = a.gpb, n = a.n, W = a.W;
+  const uint32_t g0 = blockIdx.x * (uint32_t)gpb;
+  const int ngl = min(gpb, a.G - (int)g0);
+  const int ring = 1 << a.ring_log2, rmask = ring - 1, rlog = a.ring_log2;
+  const int slot_words = gpb * W;
+  uint32_t *st = reinterpret_cast<uint32_t *>(smem);          // [2][kResStride]
+  uint32_t *ringp = st + 2 * kResStride;                      // [ring][slot_words]
+  uint64_t *full = reinterpret_cast<uint64_t *>(ringp + (size_t)ring * slot_words);
+  uint32_t *ind = reinterpret_cast<uint32_t *>(full + ring);  // [n_props][gpb][kIndRing]
+  const int n_ind = max(a.n_props, 1) * gpb * kIndRing;
+  const int items = n * gpb;
+  for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+    const int i = idx / gpb, gl = idx - i * gpb;
+    st[idx] = gl < ngl ? a.state[(size_t)(g0 + gl) * n + i] : 0u;
+  }
+  for (int j = threadIdx.x; j < n_ind; j += blockDim.x) ind[j] = kFull;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool producer = warp == (int)(blockDim.x >> 5) - 1;
+  const uint32_t full0 = smem_u32(full), ring0 = smem_u32(ringp);
+  const uint32_t slot_bytes = (uint32_t)slot_words * 4u;
+  const uint32_t copy_bytes = (uint32_t)(ngl * W) * 4u;
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < ring; j++) mbar_init(full + j);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cta_barrier();  // tables, state and barriers ready
+  if (producer) {
+    // thread 0 of the warp: copies issued (steps 0 .. issued-1) and confirmed
+    // (0 .. waited-1); `dead` once a wait gave up
+    int issued = 0, waited = 0;
+    bool dead = false;
+    auto issue = [&](int s) {
+      const int slot = s & rmask;
+      bulk_copy(ring0 + (uint32_t)slot * slot_bytes, a.planes + ((size_t)s * a.G + g0) * W, copy_bytes,
+                full0 + 8u * slot);
+      issued = s + 1;
+    };
+    auto wait_step = [&](int s) {
+      if (dead) return;
+      if (!mbar_wait_fast(full0 + 8u * (s & rmask), (uint32_t)((s >> rlog) & 1))) {
+        atomicExch(a.status, PBN_ERR_TIMEOUT);
+        dead = true;
+        return;
+      }
+      waited = s + 1;
+    };
+    // the warp stores the indicator words of steps s0 .. s0+cnt-1 (complete)
+    // and makes their ring words ready for reuse
+    auto flush = [&](int s0, int cnt) {
+      if (a.soi_size == 0) return;
+      for (int m = 0; m < a.n_props; m++)
+        for (int g = 0; g < ngl; g++) {
+          const int sl = s0 + lane;
+          if (lane < cnt) {
+            uint32_t *word = ind + (m * gpb + g) * kIndRing + (sl & (kIndRing - 1));
+            const int64_t col = a.col0 + sl;
+            if (col >= 0)
+              a.bits[m * a.prop_stride + (int64_t)(g0 + g) * a.bits_cap + col] = *word & lane_mask(a.omega, g0 + g);
+            *word = kFull;
+          }
+        }
+    };
+    if (lane == 0) {
+      for (int s = 0; s < min(ring, a.steps); s++) issue(s);
+      wait_step(0);
+    }
+    cta_barrier();  // the words of step 0 landed
+    for (int s = 0; s < a.steps; s++) {
+      if (lane == 0) {
+        if (s >= 1 && !dead && s - 1 + ring < a.steps) issue(s - 1 + ring);  // the slot step s-1 used
+        if (s + 1 < a.steps) wait_step(s + 1);
+      }
+      __syncwarp();
+      if (s > 0 && (s & 31) == 0) flush(s - 32, 32);  // steps s-32 .. s-1 are complete
+      cta_barrier();  // state after step s complete; the words of step s+1 landed
+    }
+    const int done = ((a.steps - 1) >> 5) << 5;  // steps already stored
+    flush(done, a.steps - done);
+    // every issued copy has landed before the CTA's shared memory goes away
+    if (lane == 0)
+      for (int s = waited; s < issued; s++)
+        if (!mbar_wait_fast(full0 + 8u * (s & rmask), (uint32_t)((s >> rlog) & 1))) {
+          atomicExch(a.status, PBN_ERR_TIMEOUT);
+          break;
+        }
+    return;
+  }
+  // this thread: function slot f of item it
+  const int it = threadIdx.x >> 1, f = threadIdx.x & 1;
+  const int r = it / gpb, gl = it - r * gpb;
+  const bool active = it < items && gl < ngl;
+  const uint32_t rec = active ? a.node[r] : 0u;
+  const int L = active ? node_l(rec) : 0;
+  const int f0 = node_f0(rec);
+  const int idx = node_id(rec) * gpb + gl;
+  const uint32_t vmask = active ? lane_mask(a.omega, g0 + gl) : 0u;
+  const uint32_t st0 = smem_u32(st);
+  const uint32_t own = st0 + 4u * (uint32_t)(active ? idx : 0);
+  const uint32_t woff = active ? 4u * (uint32_t)(gl * W + f0) : 0u;  // the item's words within a slot
+  const uint32_t aoff = active ? 4u * (uint32_t)(gl * W + a.F) : 0u; // the group's OR of perturbed lanes
+  const bool writer = active && f == 0;
+  ResidentFn R;
+  if (f < L) R.load(a.fn[f0 + f], st0, gpb, gl);
+  else R.clear(st0);
+  const int LW = (int)__reduce_max_sync(kFull, (unsigned)L);
+  // bit m: property m needs this node at 1 (need1) and/or at 0 (need0; both
+  // when a property names it twice)
+  uint32_t need1 = 0u, need0 = 0u;
+  if (writer)
+    for (int e = 0; e < a.soi_size; e++)
+      if ((int)a.soi_node[e] == node_id(rec)) {
+        const uint32_t bit = 1u << a.soi_prop[e];
+        if ((a.soi_val >> e) & 1u) need1 |= bit;
+        else need0 |= bit;
+      }
+  const uint32_t in_props = need1 | need0;
+  // this item's indicator words: property m, step s at ind_me + 4 (m gpb kIndRing + s % kIndRing)
+  const uint32_t ind_me = smem_u32(ind) + 4u * (uint32_t)(gl * kIndRing);
+  cta_barrier();  // the words of step 0 landed
+  // one transition: state buffer CUR (0 or 1) to the other
+  auto step = [&](int s, auto cur_tag) {
+    constexpr int CUR = decltype(cur_tag)::value;
+    constexpr int OFF_CUR = CUR * kResStride * 4, OFF_NXT = (1 - CUR) * kResStride * 4;
+    {
+      const uint32_t w = ring0 + (uint32_t)(s & rmask) * slot_bytes + woff;
+      const uint32_t P = lds_u32(w);
+      const uint32_t S1 = L > 1 ? lds_u32(w + 4u) : 0u;  // lanes of function 0 (L > 1)
+      const uint32_t old = writer ? lds_u32_at<OFF_CUR>(own) : 0u;
+      const uint32_t v = R.eval<OFF_CUR>();
+      const uint32_t rest = vmask & ~P;  // lanes that take one of the functions
+      uint32_t part;
+      if (!REST || LW <= 2) {
+        // f = 0: function 0's lanes (all of `rest` when L = 1); f = 1: the others
+        const uint32_t sel = f == 0 ? (L > 1 ? S1 : rest) : (L == 2 ? rest & ~S1 : 0u);
+        part = sel & v;
+      } else {
+        part = rest_part(w, L, LW, f, rest, v, st0 + (uint32_t)OFF_CUR, a.fn, f0, a.gpb, gl);
+      }
+      const uint32_t fword = part | __shfl_xor_sync(kFull, part, 1);
+      uint32_t nv;
+      if (MODE == PBN_PERTURB_PER_NODE) {
+        nv = (P & ~old) | fword;
+      } else {
+        const uint32_t any = lds_u32(ring0 + (uint32_t)(s & rmask) * slot_bytes + aoff);
+        nv = (any & (old ^ P)) | (~any & fword);
+      }
+      if (writer) sts_u32_at<OFF_NXT>(own, nv);
+      for (uint32_t props = in_props; props; props &= props - 1) {
+        const int m = __ffs(props) - 1;
+        const uint32_t term = ((need1 >> m) & 1u ? nv : kFull) & ((need0 >> m) & 1u ? ~nv : kFull);
+        atom_and_shared(ind_me + 4u * (uint32_t)(m * gpb * kIndRing + (s & (kIndRing - 1))), term);
+      }
+    }
+    cta_barrier();  // state after step s complete; the words of step s+1 landed
+  };
+  for (int s = 0; s < a.steps; s += 2) {
+    step(s, std::integral_constant<int, 0>());
+    if (s + 1 < a.steps) step(s + 1, std::integral_constant<int, 1>());
+  }
+  // the state after the last step (complete since its barrier)
+  if (writer) a.state[(size_t)(g0 + gl) * n + node_id(rec)] = st[(a.steps & 1) * kResStride + idx];
+}
+
+template <int MODE, bool REST>
+static cudaError_t launch_resident_mode(const SimArgs &a, int blocks, int threads, size_t smem, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(apply_resident_kernel<MODE, REST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sim_max_smem());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  apply_resident_kernel<MODE, REST><<<blocks, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_resident(const SimArgs &a, int mode, bool rest, int threads, size_t smem, cudaStream_t s) {
+  const int blocks = (a.G + a.gpb - 1) / a.gpb;
+  if (blocks == 0 || a.steps == 0) return cudaSuccess;
+  if (threads % 32 || threads < 64 || threads > 2 * kResidentItems + 32 || 2 * a.n * a.gpb > threads - 32 ||
+      a.ring_log2 < 2 || a.ring_log2 > 4 || a.has_wide)
+    return cudaErrorInvalidValue;
+  if (mode == PBN_PERTURB_PER_NODE)
+    return rest ? launch_resident_mode<PBN_PERTURB_PER_NODE, true>(a, blocks, threads, smem, s)
+                : launch_resident_mode<PBN_PERTURB_PER_NODE, false>(a, blocks, threads, smem, s);
+  return rest ? launch_resident_mode<PBN_PERTURB_GLOBAL, true>(a, blocks, threads, smem, s)
+              : launch_resident_mode<PBN_PERTURB_GLOBAL, false>(a, blocks, threads, smem, s);
+}
+
+// pad: dynamic shared memory the kernel does not use, requested only to
+// limit where its blocks may run (see run_select_ahead).
 template <int MODE, int BPR>
-static cudaError_t launch_select_variant(const SimArgs &a, cudaStream_t s) {
+static cudaError_t launch_select_variant(const SimArgs &a, size_t pad, cudaStream_t s) {
   const int64_t total = (int64_t)a.steps * a.G * a.n;
   const int threads = 256;
   const int64_t blocks = (total + threads - 1) / threads;
   if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  select_kernel<MODE, BPR><<<(unsigned)blocks, threads, 0, s>>>(a);
+  static bool attr = false;
+  if (pad > 0 && !attr) {
+    cudaError_t e = cudaFuncSetAttribute(select_kernel<MODE, BPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         sim_max_smem());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  select_kernel<MODE, BPR><<<(unsigned)blocks, threads, pad, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_select(const SimArgs &a, int mode, int BPR, cudaStream_t s) {
+cudaError_t launch_select(const SimArgs &a, int mode, int BPR, cudaStream_t s, size_t pad) {
   if (a.steps == 0 || a.G == 0) return cudaSuccess;
+  if ((int64_t)pad > sim_max_smem()) return cudaErrorInvalidValue;
   if (mode == PBN_PERTURB_PER_NODE)
-    return BPR == 2 ? launch_select_variant<PBN_PERTURB_PER_NODE, 2>(a, s)
-                    : launch_select_variant<PBN_PERTURB_PER_NODE, 1>(a, s);
-  return BPR == 2 ? launch_select_variant<PBN_PERTURB_GLOBAL, 2>(a, s)
-                  : launch_select_variant<PBN_PERTURB_GLOBAL, 1>(a, s);
+    return BPR == 2 ? launch_select_variant<PBN_PERTURB_PER_NODE, 2>(a, pad, s)
+                    : launch_select_variant<PBN_PERTURB_PER_NODE, 1>(a, pad, s);
+  return BPR == 2 ? launch_select_variant<PBN_PERTURB_GLOBAL, 2>(a, pad, s)
+                  : launch_select_variant<PBN_PERTURB_GLOBAL, 1>(a, pad, s);
 }
 
 template <int MODE, int RING, int T, bool WIDE = false>

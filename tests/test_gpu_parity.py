@@ -128,7 +128,8 @@ SA_LAUNCHES = [dict(groups_per_block=2), dict(groups_per_block=3, threads_per_bl
                dict(groups_per_block=7, threads_per_block=1024, threads_per_item=4),
                dict(groups_per_block=7, threads_per_block=512, threads_per_item=1),
                dict(threads_per_item=1), dict(threads_per_item=2), dict(threads_per_item=2, staging="global"),
-               dict(threads_per_item=4, groups_per_block=3, threads_per_block=64)]
+               dict(threads_per_item=4, groups_per_block=3, threads_per_block=64),
+               dict(groups_per_block=4), dict(groups_per_block=4, staging="smem")]
 
 
 @pytest.mark.parametrize("mode", [0, 1])
