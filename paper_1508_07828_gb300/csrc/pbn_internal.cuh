@@ -101,7 +101,8 @@ struct SimArgs {
   int ntiles;
   int tile_bytes;
   int *status;           // device status word: PBN_ERR_TIMEOUT after a bounded wait gave up
-  int test_stall;        // test hook: never issue tile 0, so its wait must time out
+  int test_stall;        // test hook: never issue tile 0 (fused kernel) or step 0's category words
+                         // (register-resident apply), so the wait for it must time out
   int soi_size;
   uint16_t soi_node[kMaxSoi];
   uint32_t soi_val;      // bit m = required value of soi_node[m]

@@ -745,7 +745,8 @@ __global__ void __launch_bounds__(2 * kResidentItems + 32, 1) apply_resident_ker
         }
     };
     if (lane == 0) {
-      for (int s = 0; s < min(ring, a.steps); s++) issue(s);
+      for (int s = 0; s < min(ring, a.steps); s++)
+        if (!(a.test_stall && s == 0)) issue(s);  // test hook: step 0's words never arrive
       wait_step(0);
     }
     cta_barrier();  // the words of step 0 landed

@@ -3,7 +3,10 @@
 the fused simulation kernel give up after its 1 s limit, record
 PBN_ERR_TIMEOUT in the device status word and return; the host reads the
 status, a driver query reading results after such a launch fails with
-PBN_ERR_TIMEOUT, and the CUDA context stays usable."""
+PBN_ERR_TIMEOUT, and the CUDA context stays usable.  The same hook keeps the
+register-resident apply kernel's first bulk copy from being issued: its
+producer gives up on that step after 1 s, issues nothing more, and the
+launch ends with the same status."""
 import os
 import subprocess
 import sys
@@ -60,3 +63,38 @@ def test_stalled_tile_times_out_and_context_survives():
                        timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "timeout path ok" in r.stdout
+
+
+CHILD_RESIDENT = textwrap.dedent("""
+    import sys
+    sys.path.insert(0, {root!r})
+    import torch
+    import pbn_synth as S
+    import paper_1508_07828_gb300 as P
+    net, soi, cfg = S.mid_config()
+    N = P.pbn_load(net)
+    cs = P.ChainSet(N, 64, bits_cap=40)
+    P.pbn_init_chains(cs, 1)
+    # one select-ahead chunk: select_kernel, then the register-resident apply
+    P.pbn_run_chains(cs, 40, 1, P.PER_NODE, soi, schedule="select_ahead")
+    torch.cuda.synchronize()
+    st = P.pbn_take_device_status()
+    assert st == P.PBN_ERR_TIMEOUT, st
+    assert P.pbn_take_device_status() == 0
+    # the context is still usable: the fused schedule and plain torch work
+    P.pbn_run_chains(cs, 4, 1, P.PER_NODE, soi, schedule="fused")
+    torch.cuda.synchronize()
+    assert P.pbn_take_device_status() == 0
+    assert torch.arange(10, device="cuda").sum().item() == 45
+    print("resident timeout path ok")
+""")
+
+
+def test_stalled_bulk_copy_times_out_and_context_survives():
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    env = dict(os.environ, PBN_TEST_STALL_FIRST_TILE="1")
+    r = subprocess.run([sys.executable, "-c", CHILD_RESIDENT.format(root=ROOT)], env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "resident timeout path ok" in r.stdout
