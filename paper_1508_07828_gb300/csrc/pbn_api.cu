@@ -678,28 +678,37 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
   net->dev.max_l = max_l;
   net->dev.ntiles = (int)tiles.size() - 1;
   net->dev.tile_bytes = max_tile * 16;
-  cudaError_t e = cudaMalloc(&net->dev.d_fn, sizeof(uint4) * (size_t)F);
-  if (e == cudaSuccess) e = cudaMalloc(&net->dev.d_node, sizeof(uint32_t) * (size_t)n);
-  if (e == cudaSuccess) e = cudaMalloc(&net->dev.d_tiles, sizeof(int32_t) * tiles.size());
-  if (e == cudaSuccess)
-    e = cudaMemcpy(net->dev.d_fn, fn_sorted.data(), sizeof(uint4) * (size_t)F, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(net->dev.d_node, node_sorted.data(), sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(net->dev.d_tiles, tiles.data(), sizeof(int32_t) * tiles.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !wide_tt.empty()) {
-    net->dev.has_wide = 1;
-    e = cudaMalloc(&net->dev.d_wide_tt, sizeof(uint32_t) * wide_tt.size());
-    if (e == cudaSuccess) e = cudaMalloc(&net->dev.d_wide_par, sizeof(uint16_t) * wide_par.size());
-    if (e == cudaSuccess)
-      e = cudaMemcpy(net->dev.d_wide_tt, wide_tt.data(), sizeof(uint32_t) * wide_tt.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(net->dev.d_wide_par, wide_par.data(), sizeof(uint16_t) * wide_par.size(),
-                     cudaMemcpyHostToDevice);
+  // every table in one device allocation, filled by one copy: function
+  // records, node records, tile starts, wide tables, wide parents (each
+  // 16-byte aligned)
+  auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  const size_t o_node = up16(sizeof(uint4) * (size_t)F);
+  const size_t o_tiles = o_node + up16(sizeof(uint32_t) * (size_t)n);
+  const size_t o_wtt = o_tiles + up16(sizeof(int32_t) * tiles.size());
+  const size_t o_wpar = o_wtt + up16(sizeof(uint32_t) * wide_tt.size());
+  const size_t total = o_wpar + up16(sizeof(uint16_t) * wide_par.size());
+  std::vector<unsigned char> pack(total, 0);
+  memcpy(pack.data(), fn_sorted.data(), sizeof(uint4) * (size_t)F);
+  memcpy(pack.data() + o_node, node_sorted.data(), sizeof(uint32_t) * (size_t)n);
+  memcpy(pack.data() + o_tiles, tiles.data(), sizeof(int32_t) * tiles.size());
+  if (!wide_tt.empty()) {
+    memcpy(pack.data() + o_wtt, wide_tt.data(), sizeof(uint32_t) * wide_tt.size());
+    memcpy(pack.data() + o_wpar, wide_par.data(), sizeof(uint16_t) * wide_par.size());
   }
+  cudaError_t e = cudaMalloc(&net->d_base, total);
+  if (e == cudaSuccess) e = cudaMemcpy(net->d_base, pack.data(), total, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     pbn_free(net);
     return cuda_fail(e, "staging network tables");
+  }
+  unsigned char *base = static_cast<unsigned char *>(net->d_base);
+  net->dev.d_fn = reinterpret_cast<uint4 *>(base);
+  net->dev.d_node = reinterpret_cast<uint32_t *>(base + o_node);
+  net->dev.d_tiles = reinterpret_cast<int32_t *>(base + o_tiles);
+  if (!wide_tt.empty()) {
+    net->dev.has_wide = 1;
+    net->dev.d_wide_tt = reinterpret_cast<uint32_t *>(base + o_wtt);
+    net->dev.d_wide_par = reinterpret_cast<uint16_t *>(base + o_wpar);
   }
   net->dev.table_bytes = (int64_t)F * 16 + (int64_t)n * 4 + (int64_t)wide_tt.size() * 4 + (int64_t)wide_par.size() * 2;
   *out = net;
@@ -708,11 +717,7 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
 
 void pbn_free(pbn_net *net) {
   if (!net) return;
-  if (net->dev.d_fn) cudaFree(net->dev.d_fn);
-  if (net->dev.d_node) cudaFree(net->dev.d_node);
-  if (net->dev.d_tiles) cudaFree(net->dev.d_tiles);
-  if (net->dev.d_wide_tt) cudaFree(net->dev.d_wide_tt);
-  if (net->dev.d_wide_par) cudaFree(net->dev.d_wide_par);
+  if (net->d_base) cudaFree(net->d_base);
   delete net;
 }
 

@@ -180,4 +180,5 @@ cudaError_t launch_skart_into(const pbn_chains &ch, int64_t col, int64_t kappa, 
 struct pbn_net {
   pbn::NetDev dev;
   int device = 0;
+  void *d_base = nullptr;  // the one device allocation holding every table of dev
 };

@@ -542,6 +542,15 @@ __device__ __forceinline__ void atom_and_shared(uint32_t addr, uint32_t v) {
   asm volatile("atom.shared.and.b32 _, [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
+// Three-input bitwise function with truth table LUT over (a, b, c) = (0xF0,
+// 0xCC, 0xAA): one instruction for a multiplexer level.
+template <int LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+  return d;
+}
+
 // CTA-wide barrier in its non-aligned form: the producer warp and the item
 // warps reach it from different loops.
 __device__ __forceinline__ void cta_barrier() { asm volatile("barrier.sync 0;" ::: "memory"); }
@@ -605,10 +614,10 @@ struct ResidentFn {
   template <int M, int Q>
   __device__ __forceinline__ uint32_t sub(const uint32_t (&x)[5]) const {
     if constexpr (M == 1) {
-      return lo[Q] ^ (x[0] & dx[Q]);
+      return lop3<0x6A>(x[0], dx[Q], lo[Q]);  // lo ^ (x0 & dx)
     } else {
       const uint32_t a = sub<M - 1, Q>(x), b = sub<M - 1, Q + (1 << (M - 2))>(x);
-      return (x[M - 1] & b) | (~x[M - 1] & a);
+      return lop3<0xCA>(x[M - 1], b, a);  // x ? b : a, bitwise
     }
   }
 

@@ -73,7 +73,7 @@ CHILD_RESIDENT = textwrap.dedent("""
     import paper_1508_07828_gb300 as P
     net, soi, cfg = S.mid_config()
     N = P.pbn_load(net)
-    cs = P.ChainSet(N, 64, bits_cap=40)
+    cs = P.ChainSet(N, 64, bits_cap=64)
     P.pbn_init_chains(cs, 1)
     # one select-ahead chunk: select_kernel, then the register-resident apply
     P.pbn_run_chains(cs, 40, 1, P.PER_NODE, soi, schedule="select_ahead")
