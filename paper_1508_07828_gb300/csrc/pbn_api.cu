@@ -800,9 +800,13 @@ int pbn_skart(const pbn_chains *ch, int64_t start, int64_t kappa, int64_t bpc, i
 namespace {
 
 // Device result slot of a driver query: one statistics result per property,
-// then the device status word, read back with one copy each.
+// the two-state results launched together with a Gelman & Rubin check at
+// kAheadOffset, then the device status word.
 constexpr size_t kResultBytes = 4096;
+constexpr size_t kAheadOffset = 2048;
 constexpr size_t kStatusOffset = kResultBytes - 64;
+static_assert(sizeof(pbn_gr_result) * PBN_MAX_PROPERTIES <= kAheadOffset, "result slot");
+static_assert(kAheadOffset + sizeof(pbn_two_state_result) * PBN_MAX_PROPERTIES <= kStatusOffset, "result slot");
 
 // Per-(device, stream) driver workspace, kept across queries so that a query
 // makes no allocation once the buffers have grown to its size: statistics
@@ -962,18 +966,21 @@ struct Query {
 
   // Result of the last statistics launch, read together with the device
   // status word (one synchronisation): a bounded wait that gave up during
-  // the query fails it here.
+  // the query fails it here.  ahead: also the two-state results at
+  // kAheadOffset (count of them), in the same copy.
   template <typename T>
-  int fetch(T *h, int count = 1) {
+  int fetch(T *h, int count = 1, pbn_two_state_result *ahead = nullptr) {
     static_assert(sizeof(T) * PBN_MAX_PROPERTIES <= kStatusOffset, "result slot");
     int *status = pbn::device_status();
     if (!status) return fail(PBN_ERR_CUDA, "device status word unavailable");
-    CUDA_TRY(cudaMemcpyAsync(ws.h_res, d_res, sizeof(T) * count, cudaMemcpyDeviceToHost, s), "result copy");
+    const size_t bytes = ahead ? kAheadOffset + sizeof(pbn_two_state_result) * count : sizeof(T) * count;
+    CUDA_TRY(cudaMemcpyAsync(ws.h_res, d_res, bytes, cudaMemcpyDeviceToHost, s), "result copy");
     CUDA_TRY(cudaMemcpyAsync((char *)ws.h_res + kStatusOffset, status, sizeof(int), cudaMemcpyDeviceToHost, s),
              "status copy");
     CUDA_TRY(cudaStreamSynchronize(s), "stream sync");
     memcpy(h, ws.h_res, sizeof(T) * count);
-    d2h_bytes += sizeof(T) * count + sizeof(int);
+    if (ahead) memcpy(ahead, (char *)ws.h_res + kAheadOffset, sizeof(pbn_two_state_result) * count);
+    d2h_bytes += bytes + sizeof(int);
     int st = 0;
     memcpy(&st, (char *)ws.h_res + kStatusOffset, sizeof st);
     if (st) {
@@ -990,10 +997,20 @@ struct Query {
     return v;
   }
 
+  // Two-state statistics (Alg. 3's first check) launched with every Gelman &
+  // Rubin check on the same window [psi, 2 psi) and read in the same
+  // synchronisation: when R-hat converges, Alg. 3 starts on exactly that
+  // window, so its first round needs no launch or read of its own.
+  struct TwoStateAhead {
+    double eps = 0, r = 0, s = 0;
+    bool valid = false;  // results of the window [psi, 2 psi) of the returned psi
+    pbn_two_state_result res[PBN_MAX_PROPERTIES];
+  };
+
   // Alg. GR; with several properties psi doubles until every property's
   // R-hat is below the threshold (*rhat: the largest, rhat_each[m]: each).
   int gelman_rubin(int64_t psi0, double thr, int64_t max_length, int64_t *psi_out, double *rhat, int32_t *rounds,
-                   double *rhat_each = nullptr) {
+                   double *rhat_each = nullptr, TwoStateAhead *ahead = nullptr) {
     const int q = std::max(1, n_recorded_props(cfg));
     int64_t psi = psi0;
     *rounds = 0;
@@ -1005,8 +1022,16 @@ struct Query {
         CUDA_TRY(pbn::launch_gelman_rubin(view(m), psi - ch.bits_base, psi, (pbn_gr_result *)d_res + m, sc, s),
                  "G&R");
       stat_launched(q);
+      if (ahead) {
+        for (int m = 0; m < q; m++)
+          CUDA_TRY(pbn::launch_two_state(view(m), psi - ch.bits_base, psi, ahead->eps, ahead->r, ahead->s,
+                                         (pbn_two_state_result *)((char *)d_res + kAheadOffset) + m, sc, s),
+                   "two-state");
+        stat_launched(q);
+      }
       pbn_gr_result r[PBN_MAX_PROPERTIES];
-      if ((rc = fetch(r, q))) return rc;
+      if ((rc = fetch(r, q, ahead ? ahead->res : nullptr))) return rc;
+      if (ahead) ahead->valid = true;
       (*rounds)++;
       bool all = true;
       double worst = -INFINITY;
@@ -1102,8 +1127,12 @@ int two_state_driver(const pbn_net *net, const pbn_two_state_query *q, int n_pro
   if ((rc = Q.open(q->omega))) return rc;
   int64_t psi;
   double rhat_each[PBN_MAX_PROPERTIES];
+  Query::TwoStateAhead ahead;
+  ahead.eps = q->eps;
+  ahead.r = q->r;
+  ahead.s = q->s;
   if ((rc = Q.gelman_rubin(q->psi0, q->rhat_threshold, q->max_length, &psi, &out->rhat, &out->gr_rounds,
-                           rhat_each)))
+                           rhat_each, &ahead)))
     return rc;
   out->gr_psi = psi;
   const int64_t omega = q->omega;
@@ -1117,13 +1146,19 @@ int two_state_driver(const pbn_net *net, const pbn_two_state_query *q, int n_pro
         if ((rc = Q.extend_to(psi + 2, psi))) return rc;
         continue;
       }
-      for (int m = 0; m < np; m++)
-        CUDA_TRY(pbn::launch_two_state(Q.view(m), psi - Q.ch.bits_base, n, q->eps, q->r, q->s,
-                                       (pbn_two_state_result *)Q.d_res + m, Q.sc, Q.s),
-                 "two-state");
-      Q.stat_launched(np);
       pbn_two_state_result got[PBN_MAX_PROPERTIES];
-      if ((rc = Q.fetch(got, np))) return rc;
+      if (ahead.valid && n == psi) {
+        // the window of the converged Gelman & Rubin check: read with it
+        memcpy(got, ahead.res, sizeof(pbn_two_state_result) * np);
+      } else {
+        for (int m = 0; m < np; m++)
+          CUDA_TRY(pbn::launch_two_state(Q.view(m), psi - Q.ch.bits_base, n, q->eps, q->r, q->s,
+                                         (pbn_two_state_result *)Q.d_res + m, Q.sc, Q.s),
+                   "two-state");
+        Q.stat_launched(np);
+        if ((rc = Q.fetch(got, np))) return rc;
+      }
+      ahead.valid = false;
       out->ts_rounds++;
       bool insufficient = false;
       for (int m = 0; m < np; m++) insufficient |= got[m].status == PBN_ERR_INSUFFICIENT;
