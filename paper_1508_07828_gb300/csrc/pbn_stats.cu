@@ -14,52 +14,73 @@ namespace pbn {
 
 // ------------------------------------------------------------ Gelman-Rubin
 
+// One block per chain group (blocks loop over groups when there are more):
+// its 8 warps split the window's columns, each warp counting the ones of its
+// columns per chain (bit-transpose + popc, lane = chain); the per-chain
+// counts c_i are summed over the warps in shared memory, then S1 = sum c_i and
+// S2 = sum c_i^2 (128-bit) over the group's valid chains.
 __global__ void __launch_bounds__(256) gr_kernel(const uint32_t *bits, int64_t cap, int64_t col, int64_t psi,
                                                  int64_t omega, int G, unsigned long long *partials,
                                                  unsigned int *ticket, pbn_gr_result *out) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  uint64_t acc[3] = {0, 0, 0};  // S1, S2 lo, S2 hi
-  for (int64_t g = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); g < G; g += (int64_t)gridDim.x * wpb) {
+  __shared__ uint32_t cnt_s[8][32];
+  // columns of the window per warp: a multiple of 32
+  const int64_t per_warp = ((psi + wpb - 1) / wpb + 31) / 32 * 32;
+  uint64_t acc1 = 0;
+  u128 acc2 = 0;
+  for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
     const uint32_t *row = bits + (size_t)g * cap + col;
     uint32_t cnt = 0;
-    for (int64_t j = 0; j < psi; j += 32) {
-      const uint32_t w = (j + lane < psi) ? row[j + lane] : 0u;
-      cnt += __popc(warp_transpose32(w, lane));
+    const int64_t j0 = (int64_t)w * per_warp, j1 = min(psi, j0 + per_warp);
+    for (int64_t j = j0; j < j1; j += 32) {
+      const uint32_t v = (j + lane < j1) ? row[j + lane] : 0u;
+      cnt += __popc(warp_transpose32(v, lane));
     }
-    if (!((group_lanes(omega, g) >> lane) & 1u)) cnt = 0;
-    const uint64_t s1 = warp_sum<uint64_t>(cnt);
-    const u128 s2 = warp_sum_u128((u128)((uint64_t)cnt * cnt));
-    if (lane == 0) {
-      acc[0] += s1;
-      u128 t = ((u128)acc[2] << 64 | acc[1]) + s2;
-      acc[1] = (uint64_t)t;
-      acc[2] = (uint64_t)(t >> 64);
+    cnt_s[w][lane] = cnt;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t c = 0;
+      for (int k = 0; k < wpb; k++) c += cnt_s[k][lane];
+      if (!((group_lanes(omega, g) >> lane) & 1u)) c = 0;
+      const uint64_t s1 = warp_sum<uint64_t>(c);
+      const u128 s2 = warp_sum_u128((u128)((uint64_t)c * c));
+      if (lane == 0) {
+        acc1 += s1;
+        acc2 += s2;
+      }
     }
+    __syncthreads();  // cnt_s reused by the next group
   }
-  // block sum of (S1, S2) where S2 is held as 128-bit (lo, hi) pairs
-  __shared__ u128 red2[32];
-  __shared__ uint64_t red1[32];
-  const int w = threadIdx.x >> 5;
-  if (lane == 0) {
-    red1[w] = acc[0];
-    red2[w] = ((u128)acc[2] << 64) | acc[1];
-  }
-  __syncthreads();
   uint64_t part[3] = {0, 0, 0};
   if (threadIdx.x == 0) {
-    uint64_t s1 = 0;
-    u128 s2 = 0;
-    for (int k = 0; k < wpb; k++) { s1 += red1[k]; s2 += red2[k]; }
-    part[0] = s1; part[1] = (uint64_t)s2; part[2] = (uint64_t)(s2 >> 64);
+    part[0] = acc1;
+    part[1] = (uint64_t)acc2;
+    part[2] = (uint64_t)(acc2 >> 64);
   }
   if (!publish_partials<3>(part, partials, ticket)) return;
-  if (threadIdx.x != 0) return;
+  // the last block folds the partials, every thread a strided share
   uint64_t S1 = 0;
   u128 S2 = 0;
-  for (unsigned b = 0; b < gridDim.x; b++) {
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
     S1 += partials[(size_t)b * 3];
     S2 += ((u128)partials[(size_t)b * 3 + 2] << 64) | partials[(size_t)b * 3 + 1];
+  }
+  S1 = warp_sum<uint64_t>(S1);
+  S2 = warp_sum_u128(S2);
+  __shared__ uint64_t f1[8];
+  __shared__ u128 f2[8];
+  if (lane == 0) {
+    f1[w] = S1;
+    f2[w] = S2;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  S1 = 0;
+  S2 = 0;
+  for (int k = 0; k < wpb; k++) {
+    S1 += f1[k];
+    S2 += f2[k];
   }
   *ticket = 0u;
   pbn_gr_result r;
@@ -95,10 +116,12 @@ __global__ void __launch_bounds__(256) two_state_kernel(const uint32_t *bits, in
   }
   block_sum64<4>(v);
   if (!publish_partials<4>(v, partials, ticket)) return;
-  if (threadIdx.x != 0) return;
+  // the last block folds the partials, every thread a strided share
   uint64_t t[4] = {0, 0, 0, 0};
-  for (unsigned b = 0; b < gridDim.x; b++)
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
     for (int k = 0; k < 4; k++) t[k] += partials[(size_t)b * 4 + k];
+  block_sum64<4>(t);
+  if (threadIdx.x != 0) return;
   *ticket = 0u;
   pbn_two_state_result r;
   r.n11 = (int64_t)t[0];
@@ -286,9 +309,8 @@ cudaError_t scratch_reserve_batches(StatsScratch &sc, int64_t count, cudaStream_
 cudaError_t launch_gelman_rubin(const pbn_chains &ch, int64_t col, int64_t psi, pbn_gr_result *out,
                                 StatsScratch &sc, cudaStream_t s) {
   const int G = (int)((ch.omega + 31) / 32);
-  const int threads = 256;
-  const int blocks = stat_blocks(G, threads / 32);
-  gr_kernel<<<blocks, threads, 0, s>>>(ch.bits, ch.bits_cap, col, psi, ch.omega, G, sc.partials, sc.ticket, out);
+  const int blocks = (int)std::min<int64_t>(std::max(G, 1), kMaxStatBlocks);  // one block per group
+  gr_kernel<<<blocks, 256, 0, s>>>(ch.bits, ch.bits_cap, col, psi, ch.omega, G, sc.partials, sc.ticket, out);
   return cudaGetLastError();
 }
 
