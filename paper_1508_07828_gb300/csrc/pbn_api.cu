@@ -400,18 +400,23 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
   // with the latency-bound apply, which keeps its issue slots.
   size_t select_pad = 0, apply_smem = sp.smem;
   if (pipe && (G + sp.gpb - 1) / sp.gpb < sm_count()) {
-    int dev = 0, per_sm = 0, reserved = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) {
+    static int per_sm = -1, reserved = -1;  // device attributes, read once
+    if (per_sm < 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = reserved = 0;
+      }
+    }
+    if (per_sm > 0) {
       const int64_t pad = per_sm / 4 - reserved;
       const int64_t need = (int64_t)per_sm - pad - 2 * reserved + 16;
       if (pad > 0 && need <= pbn::sim_max_smem()) {
         select_pad = (size_t)pad;
         apply_smem = std::max(apply_smem, (size_t)need);
       }
-    } else {
-      cudaGetLastError();
     }
   }
   LaunchPlan lp;
@@ -882,6 +887,7 @@ struct Query {
   size_t n_events = 0;   // events 0, 1: whole query; then start/stop pairs of simulation launches
   int64_t sim_launches = 0, kernel_launches = 0, sim_items = 0, d2h_bytes = 0;
   ApplyTiming apply_timing;
+  bool unchecked = false;  // simulation launched since the status word was last read
 
   Query(const pbn::NetDev &n, cudaStream_t st)
       : net(n), s(st), ws(workspace_for(st)), hold(ws.mu), sc(ws.sc) {
@@ -955,6 +961,7 @@ struct Query {
     CUDA_TRY(cudaEventRecord(b, s), "event");
     sim_launches += launches;
     kernel_launches += launches;
+    unchecked = true;
     sim_items += steps * (int64_t)net.n * ((ch.omega + 31) / 32);
     return PBN_OK;
   }
@@ -974,6 +981,7 @@ struct Query {
     int *status = pbn::device_status();
     if (!status) return fail(PBN_ERR_CUDA, "device status word unavailable");
     const size_t bytes = ahead ? kAheadOffset + sizeof(pbn_two_state_result) * count : sizeof(T) * count;
+    CUDA_TRY(cudaEventRecord(ws.events[1], s), "event");  // the query's device time so far
     CUDA_TRY(cudaMemcpyAsync(ws.h_res, d_res, bytes, cudaMemcpyDeviceToHost, s), "result copy");
     CUDA_TRY(cudaMemcpyAsync((char *)ws.h_res + kStatusOffset, status, sizeof(int), cudaMemcpyDeviceToHost, s),
              "status copy");
@@ -983,10 +991,23 @@ struct Query {
     d2h_bytes += bytes + sizeof(int);
     int st = 0;
     memcpy(&st, (char *)ws.h_res + kStatusOffset, sizeof st);
+    unchecked = false;
     if (st) {
       CUDA_TRY(cudaMemset(status, 0, sizeof st), "status clear");
       return fail(st, "a bounded device wait gave up during the query");
     }
+    return PBN_OK;
+  }
+
+  // End of a query: a bounded wait that gave up in a launch after the last
+  // result read fails the query (the reads check the status word themselves).
+  int final_status() {
+    if (!unchecked) return PBN_OK;
+    int st = 0;
+    int rc = take_status(&st);
+    if (rc) return rc;
+    if (st) return fail(st, "a bounded device wait gave up during the query");
+    unchecked = false;
     return PBN_OK;
   }
 
@@ -1046,10 +1067,15 @@ struct Query {
     }
   }
 
+  // Device time of the query: from its first launch to the last result read
+  // (event 1 is recorded with every read, which synchronises after it), or
+  // to now when launches followed the last read.
   double elapsed_ms() {
     float ms = 0.f;
-    cudaEventRecord(ws.events[1], s);
-    cudaEventSynchronize(ws.events[1]);
+    if (unchecked) {
+      cudaEventRecord(ws.events[1], s);
+      cudaEventSynchronize(ws.events[1]);
+    }
     cudaEventElapsedTime(&ms, ws.events[0], ws.events[1]);
     return ms;
   }
@@ -1202,11 +1228,7 @@ int two_state_driver(const pbn_net *net, const pbn_two_state_query *q, int n_pro
     e.ones = r[m].ones;
     e.n4[0] = r[m].n00; e.n4[1] = r[m].n01; e.n4[2] = r[m].n10; e.n4[3] = r[m].n11;
   }
-  {
-    int st = 0;
-    if ((rc = take_status(&st))) return rc;
-    if (st) return fail(st, "a bounded device wait gave up during the query");
-  }
+  if ((rc = Q.final_status())) return rc;
   out->psi = psi;
   out->length = Q.ch.length;
   out->sample_size = omega * (Q.ch.length - psi);
@@ -1283,11 +1305,7 @@ extern "C" int pbn_estimate_two_state_seq(const pbn_net *net, const pbn_two_stat
            "two-state");
   Q.stat_launched(1);
   if ((rc = Q.fetch(&r))) return rc;
-  {
-    int st = 0;
-    if ((rc = take_status(&st))) return rc;
-    if (st) return fail(st, "a bounded device wait gave up during the query");
-  }
+  if ((rc = Q.final_status())) return rc;
   out->ones = r.ones;
   out->prob = (double)r.ones / (double)N;
   out->M = M;
@@ -1390,11 +1408,7 @@ extern "C" int pbn_estimate_skart_seq(const pbn_net *net, const pbn_skart_query 
     kappa = k1;
     pp = p1;
   }
-  {
-    int st = 0;
-    if ((rc = take_status(&st))) return rc;
-    if (st) return fail(st, "a bounded device wait gave up during the query");
-  }
+  if ((rc = Q.final_status())) return rc;
   out->psi = d * kappa;
   out->length = Q.ch.length;
   out->kappa = kappa;
@@ -1486,11 +1500,7 @@ extern "C" int pbn_estimate_skart(const pbn_net *net, const pbn_skart_query *q, 
     p = cdiv(p1, omega) * omega;
     eta = kappa * p;
   }
-  {
-    int st = 0;
-    if ((rc = take_status(&st))) return rc;
-    if (st) return fail(st, "a bounded device wait gave up during the query");
-  }
+  if ((rc = Q.final_status())) return rc;
   out->psi = psi;
   out->length = Q.ch.length;
   out->kappa = kappa;
