@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--serve", action="store_true", help="Poisson arrivals over a pool of 200 networks")
     ap.add_argument("--seq", action="store_true",
                     help="sequential Alg. 1 on one chain against the parallel query (speed-up, speed-up E)")
+    ap.add_argument("--seq-runs", type=int, default=3, help="sequential/parallel pairs of --seq")
     ap.add_argument("--seq-r", type=float, default=1e-4,
                     help="precision r of the --seq comparison (the paper's experiments use 1e-4)")
     ap.add_argument("--sweep", action="store_true", help="the paper's n x density sweep at precision --seq-r")
@@ -628,7 +629,7 @@ def run_seq(args):
     timed(lambda: P.pbn_estimate_two_state(N, soi, seed=1, **par_kw))
     timed(lambda: P.pbn_estimate_two_state_seq(N, soi, seed=1, **seq_kw))
     rows = []
-    for k in range(args.steps):
+    for k in range(args.seq_runs):
         tp, rp = timed(lambda: P.pbn_estimate_two_state(N, soi, seed=100 + k, **par_kw))
         ts, rs = timed(lambda: P.pbn_estimate_two_state_seq(N, soi, seed=200 + k, **seq_kw))
         sp = ts / tp

@@ -255,13 +255,13 @@ int grow(uint32_t *&buf, size_t &have, size_t words, cudaStream_t s) {
   return PBN_OK;
 }
 
-// Largest chunk of the select-ahead schedule: 1024 steps, or fewer when the
+// Largest chunk of the select-ahead schedule: 2048 steps, or fewer when the
 // category words of all groups would exceed 32 MiB per buffer (both buffers
 // of a pipelined run stay in L2 between the kernels at the chain counts this
 // schedule is for).  A run longer than one chunk starts with kSelectFirst
 // steps and doubles the chunk up to the largest, so the first apply starts
 // early and every later chunk is drawn while the previous one is applied.
-constexpr int64_t kSelectMaxSteps = 1024;
+constexpr int64_t kSelectMaxSteps = 2048;
 constexpr int64_t kSelectBudgetBytes = 32ll << 20;
 constexpr int64_t kSelectFirst = 128;
 
@@ -428,7 +428,10 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
   lp.staging = sp.staging;
   int64_t k = 0;
   for (int64_t done = 0, i = 0; done < steps; done += k, i++) {
+    // ramp 128, 256, 512, then chunks of C; from the fourth on, a rest that
+    // fits one chunk is taken whole (it is drawn while 512 or more steps apply)
     k = pipe ? std::min(std::min(C, kSelectFirst << std::min<int64_t>(i, 20)), steps - done) : steps - done;
+    if (pipe && i >= 3 && steps - done <= C) k = steps - done;
     const int b = pipe ? (int)(i & 1) : 0;
     cudaStream_t ss = pipe ? sc->side : s;
     pbn::SimArgs a = make_args(net, cfg, ch, k, lp);
