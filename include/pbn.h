@@ -139,12 +139,16 @@ typedef struct pbn_run_cfg {
  * and updates it, step by step.  SELECT_AHEAD: a first kernel draws the
  * categories of a chunk of steps for all chains at once (they do not depend
  * on the state), a second applies them step by step; for few chain groups,
- * where the fused step waits on its Philox rounds with most SMs idle.
- * SELECT_AHEAD takes staging 0, 1 or 3 and needs device scratch of up to
- * 64 MiB per stream (kept by the library, grown on demand).  AUTO: select-ahead
- * when the chain groups (ceil(omega / 32)) number at most the SMs, the network
- * has at most 1000 nodes or the groups at most half the SMs, and its shared
- * memory fits; else fused. */
+ * where the fused step waits on its Philox rounds with most SMs idle.  A run
+ * longer than one chunk draws chunk i+1 on a library-owned side stream while
+ * chunk i is applied on the caller's stream; events order the two, so the
+ * call stays stream-ordered on the caller's stream (and can be captured in a
+ * CUDA graph like any fork and join).  SELECT_AHEAD takes staging 0, 1 or 3
+ * and needs device scratch of up to two 32 MiB buffers per stream (kept by
+ * the library, grown on demand).  AUTO: select-ahead when the chain groups
+ * (ceil(omega / 32)) number at most the SMs, the network has at most 1000
+ * nodes or the groups at most half the SMs, and its shared memory fits; else
+ * fused. */
 enum { PBN_SCHEDULE_AUTO = 0, PBN_SCHEDULE_FUSED = 1, PBN_SCHEDULE_SELECT_AHEAD = 2 };
 
 /* ---------------------------------------------------------------- network */

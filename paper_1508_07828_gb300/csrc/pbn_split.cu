@@ -5,10 +5,11 @@
 // predictor function j) depends on (seed, node, t, chain) only, never on the
 // state.  So the draws of every (step, chain group, node) of a chunk of steps
 // are independent work: select_kernel spreads them over the whole GPU.  What
-// stays sequential is the state update proper, which apply_kernel runs with
-// one CTA per chain group(s): per step a thread reads its item's category
-// words, evaluates the selected truth tables on the parents' words and writes
-// the next state; one barrier per step.  When few chain groups exist (a query
+// stays sequential is the state update proper, which apply_resident_kernel
+// (or apply_kernel for the shapes it does not take) runs with one CTA per
+// chain group(s): per step a thread reads its item's category words,
+// evaluates the selected truth tables on the parents' words and writes the
+// next state; one barrier per step.  When few chain groups exist (a query
 // of about a thousand chains) the fused kernel leaves most SMs idle and waits
 // on a chain of Philox rounds every step; here the Philox work runs at full
 // width and the sequential part is short.
