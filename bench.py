@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="64 networks of uneven size: the engine vs the plain one-query-at-a-time loop")
     ap.add_argument("--serve", action="store_true", help="Poisson arrivals over a pool of 200 networks")
+    ap.add_argument("--skart-large", action="store_true",
+                    help="Alg. GR + Alg. 4 (Skart) on the large network: n = 2000, 16384 chains, relative 0.01")
     ap.add_argument("--seq", action="store_true",
                     help="sequential Alg. 1 on one chain against the parallel query (speed-up, speed-up E)")
     ap.add_argument("--seq-runs", type=int, default=3, help="sequential/parallel pairs of --seq")
@@ -238,6 +240,32 @@ def oracle_sample(net, soi, omega, target_s=12.0):
     dt = time.perf_counter() - t
     upd = omega * steps * net.n
     return upd / dt, steps, dt
+
+
+def _oracle_worker(job):
+    """One host process of oracle_all_cores: its share of the chains for a
+    fixed number of transitions; returns the seconds the simulation took."""
+    net, omega_w, steps, soi = job
+    import oracle
+    st = oracle.init_states(net, 99, omega_w)
+    t = time.perf_counter()
+    oracle.simulate(net, 0, 99, st, 0, steps, soi)
+    return time.perf_counter() - t
+
+
+def oracle_all_cores(net, soi, omega, rate_one_core, target_s=8.0):
+    """The same oracle on every host core at once: the chains split over
+    os.cpu_count() processes (spawned, so none inherits a CUDA context), each
+    simulating its share for a number of transitions sized to about target_s
+    seconds at the one-core rate.  Throughput = all updates / slowest share."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    omega_w = max(1, omega // cores)
+    steps = max(2, int(target_s * rate_one_core / (omega_w * net.n)))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        times = pool.map(_oracle_worker, [(net, omega_w, steps, soi)] * cores)
+    upd = cores * omega_w * steps * net.n
+    return upd / max(times), cores, steps, omega_w, max(times)
 
 
 # ------------------------------------------------------------------- arms
@@ -425,6 +453,10 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
                                 "sample": f"oracle simulation of all {omega} chains for {steps} transitions "
                                           f"({dt:.1f} s)"}
+        va, cores, steps_a, omega_w, dta = oracle_all_cores(net, soi, omega, v)
+        line["cpu_baseline_all_cores"] = {"value": va, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                                          "sample": f"{cores} processes, {omega_w} chains each, {steps_a} "
+                                                    f"transitions ({dta:.1f} s)"}
     print(json.dumps(line))
 
 
@@ -478,6 +510,40 @@ def run_sim_only(args):
                       "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                                    "frac": achieved / peak},
                       "launch": launch}))
+
+
+def run_skart_large(args):
+    """The large workload end to end: n = 2000 scale-free network, 16384
+    chains, Gelman & Rubin (R-hat < 1.05) then Skart at relative precision
+    0.01 on nodes 0..9.  Their target values are chain 0's state after 1024
+    transitions of the GPU path itself, so the pattern has mass."""
+    import torch
+    import pbn_synth as S
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+    torch.cuda.set_device(0)
+    net, nodes, cfg = S.large_config()
+    N = P.pbn_load(net)
+    cs = P.ChainSet(N, 32, bits_cap=1)
+    P.pbn_init_chains(cs, 5)
+    P.pbn_run_chains(cs, 1024, 5, P.PER_NODE, None)
+    soi = S.StateOfInterest(nodes, cs.states_numpy()[0][nodes])
+    kw = dict(omega=cfg["omega"], H_star=cfg["rel"], relative=True, alpha=cfg["alpha"], psi0=PSI0, rhat=cfg["rhat"])
+    P.pbn_estimate_skart(N, soi, seed=1, **kw)  # warm-up
+    rows = []
+    for k in range(max(1, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = P.pbn_estimate_skart(N, soi, seed=10 + k, **kw)
+        dt = time.perf_counter() - t0
+        rows.append(dict(seconds=dt, updates_per_s=r["chain_node_updates"] / dt, length=r["length"],
+                         psi=r["psi"], sample_size=r["sample_size"], batches=r["batches"], kappa=r["kappa"],
+                         mean=r["mean"], ci=[r["ci_lo"], r["ci_hi"]], H=r["H"], sim_share=r["sim_ms"] / r["device_ms"]))
+    print(json.dumps({"mode": "skart-large", "workload": "large-n2000-omega16384-skart-rel0.01",
+                      "functions": int(net.n_functions), "runs": rows,
+                      "median_seconds": float(np.median([x["seconds"] for x in rows])),
+                      "median_updates_per_s": float(np.median([x["updates_per_s"] for x in rows]))}))
 
 
 def _percentiles(x):
@@ -773,6 +839,8 @@ def main():
     if args.batched:
         run_batched(args)
         return
+    if args.skart_large:
+        return run_skart_large(args)
     if args.serve:
         run_serve(args)
         return

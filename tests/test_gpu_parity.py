@@ -112,6 +112,27 @@ def test_item_thread_variants_bit_exact(P, name, launch):
         assert np.array_equal(cs.indicator_numpy(0, 33), ind)
 
 
+@pytest.mark.parametrize("gpb", [0, 3])
+@pytest.mark.parametrize("name", ["k0-mix", "l8", "scalefree-300", "high-p", "three-node"])
+def test_resident_apply_with_more_functions_bit_exact(P, name, gpb):
+    """The select-ahead schedule with one thread per item asked for: the
+    register-resident apply, with its path for nodes of more than two
+    functions (up to eight in l8), one or three chain groups per CTA, both
+    perturbation readings, a call that spans two chunks: the oracle's chains."""
+    net, soi, omega = next((x[1], x[2], x[3]) for x in NETS if x[0] == name)
+    for mode in (0, 1):
+        cs, init, states = _gpu_run(P, net, soi, 3 * omega, 41, mode, [37, 2100], schedule="select_ahead",
+                                    threads_per_item=1, groups_per_block=gpb)
+        ref = oracle.init_states(net, 41, 3 * omega)
+        t0, inds = 0, []
+        for k, got in zip([37, 2100], states):
+            ref, ind = oracle.simulate(net, mode, 41, ref, t0, k, soi)
+            inds.append(ind)
+            assert np.array_equal(got, ref), (name, mode, t0)
+            t0 += k
+        assert np.array_equal(cs.indicator_numpy(0, t0), np.concatenate(inds, axis=1))
+
+
 @pytest.mark.parametrize("schedule", ["fused", "select_ahead"])
 def test_max_nodes_and_max_soi(P, schedule):
     net = S.random_pbn(31, 4096, (1, 2), (0, 5), "biased", "uniform", 0.002)
