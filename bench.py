@@ -270,6 +270,23 @@ def oracle_all_cores(net, soi, omega, rate_one_core, target_s=8.0):
 
 # ------------------------------------------------------------------- arms
 
+def reduce_over_ranks(slowest, summed, world, device):
+    """Whole-job figures of N replicas: the timed durations as their maximum
+    over the ranks (the job ends with its slowest replica), the units of work
+    as their sum.  One rank: the values themselves."""
+    slowest = [float(x) for x in slowest]
+    summed = [float(x) for x in summed]
+    if world <= 1:
+        return slowest, summed
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(slowest, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor(summed, dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t], [float(x) for x in u]
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -381,16 +398,7 @@ def run_ours(args):
     total_ms = sum(times)
     upd = sum(r["chain_node_updates"] for r in reports)
     e2e_s = sum(e2e_times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([upd, e2e_upd], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_ms, e2e_s = float(t[0]), float(t[1])
-        upd_all, e2e_upd_all = float(u[0]), float(u[1])
-    else:
-        upd_all, e2e_upd_all = float(upd), float(e2e_upd)
+    (total_ms, e2e_s), (upd_all, e2e_upd_all) = reduce_over_ranks([total_ms, e2e_s], [upd, e2e_upd], world, "cuda")
     if rank != 0:
         return
 
