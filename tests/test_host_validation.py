@@ -1,0 +1,111 @@
+"""Malformed inputs are refused on the host, before any device work (so these
+run without a GPU): pbn_load's validation of the network (structure,
+probabilities, limits) and the drivers' validation of a query.  Each returns
+its status code with a message from pbn_last_error."""
+import math
+import types
+
+import numpy as np
+import pytest
+
+import pbn_synth as S
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+    return P
+
+
+def _net(**over):
+    """A valid 3-node network (the hand-built one), with fields replaced."""
+    base = S.three_node(1 / 16)
+    d = dict(n=base.n, fn_offset=base.fn_offset.copy(), par_offset=base.par_offset.copy(),
+             parents=base.parents.copy(), truth_table=base.truth_table.copy(),
+             select_prob=base.select_prob.copy(), p=base.p, tt_offset=None, tt_words=None)
+    d.update(over)
+    return types.SimpleNamespace(**d)
+
+
+def _status(P, net):
+    with pytest.raises(P.PbnError) as e:
+        P.pbn_load(net)
+    assert P.lib().pbn_last_error().decode()  # a message says why
+    return e.value.status
+
+
+def test_structure_is_checked(P):
+    assert _status(P, _net(n=0, fn_offset=np.zeros(1, np.int32))) == P.PBN_ERR_INVALID
+    fo = _net().fn_offset.copy()
+    fo[-1] += 1  # does not span the functions
+    assert _status(P, _net(fn_offset=fo)) == P.PBN_ERR_INVALID
+    par = _net().parents.copy()
+    par[0] = 3  # node 3 of a 3-node network
+    assert _status(P, _net(parents=par)) == P.PBN_ERR_INVALID
+    par[0] = -1
+    assert _status(P, _net(parents=par)) == P.PBN_ERR_INVALID
+    fo = _net().fn_offset.copy()
+    fo[1] = fo[0]  # node 0 without a predictor function
+    assert _status(P, _net(fn_offset=fo)) == P.PBN_ERR_INVALID
+
+
+def test_probabilities_are_checked(P):
+    for p in (float("nan"), -0.1, 1.0, 1.5):
+        assert _status(P, _net(p=p)) == P.PBN_ERR_INVALID, p
+    c = _net().select_prob.copy()
+    c[1] = math.nan
+    assert _status(P, _net(select_prob=c)) == P.PBN_ERR_INVALID
+    c = _net().select_prob.copy()
+    c[1] += 0.01  # node 1's probabilities no longer sum to 1
+    assert _status(P, _net(select_prob=c)) == P.PBN_ERR_INVALID
+    c = _net().select_prob.copy()
+    c[1], c[2] = 1.25, -0.25  # sums to 1, but not probabilities
+    assert _status(P, _net(select_prob=c)) == P.PBN_ERR_INVALID
+
+
+def test_limits_are_checked(P):
+    big = S.random_pbn(1, 4097, (1, 1), (1, 1), "fair", "uniform", 0.01)  # PBN_MAX_NODES + 1
+    assert _status(P, big) == P.PBN_ERR_UNSUPPORTED
+    nine = S.from_lists(1, [[((0,), 0b10, 1 / 9)] * 9], 0.01)  # nine functions on one node
+    assert _status(P, nine) == P.PBN_ERR_UNSUPPORTED
+    # a 6-input function without a multi-word table
+    six = _net(par_offset=np.array([0, 6, 7, 8, 10], np.int32),
+               parents=np.array([1, 2, 0, 1, 2, 0, 0, 2, 0, 1], np.int32))
+    six.tt_offset = None
+    assert _status(P, six) == P.PBN_ERR_INVALID
+
+
+def test_query_without_network_is_refused(P):
+    """A query on no network is refused before anything is launched (the C
+    entry point, stream NULL)."""
+    import ctypes
+    soi = P.SoiArg(S.StateOfInterest([0], [1]))
+    out = P.TwoStateReport()
+    q = P.TwoStateQuery(8, 64, 1.05, 1e-10, 0.01, 0.95, 1 << 20, 1, 0, soi.struct)
+    assert P.lib().pbn_estimate_two_state(None, ctypes.byref(q), ctypes.byref(out), None) == P.PBN_ERR_INVALID
+    assert P.lib().pbn_last_error().decode()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("bad", [dict(omega=1), dict(psi0=1), dict(r=0.0), dict(r=math.nan), dict(s=1.0),
+                                 dict(eps=0.0), dict(max_length=100), dict(rhat=0.0), dict(mode=7)],
+                         ids=lambda d: next(iter(d)))
+def test_query_parameters_are_checked(P, bad):
+    """Parameters out of range fail the query with PBN_ERR_INVALID."""
+    N = P.pbn_load(_net())
+    kw = dict(omega=8, seed=1, psi0=64, r=0.01)
+    kw.update(bad)
+    with pytest.raises(P.PbnError) as e:
+        P.pbn_estimate_two_state(N, S.StateOfInterest([0], [1]), **kw)
+    assert e.value.status == P.PBN_ERR_INVALID
+
+
+@pytest.mark.gpu
+def test_state_of_interest_is_checked(P):
+    N = P.pbn_load(_net())
+    for soi in (S.StateOfInterest([3], [1]), S.StateOfInterest([0], [2]), S.StateOfInterest([], [])):
+        with pytest.raises(P.PbnError) as e:
+            P.pbn_estimate_two_state(N, soi, omega=8, seed=1, psi0=64, r=0.01)
+        assert e.value.status == P.PBN_ERR_INVALID
