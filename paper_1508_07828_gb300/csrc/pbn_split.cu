@@ -15,15 +15,17 @@
 // width and the sequential part is short.
 //
 // Category words of item (step s, group g, processing position r) at
-// planes[(s * G + g) * W + f0_r + w], w < l_r (f0_r = the node's first
-// function record in processing order, W = F rounded up to 4 words):
+// planes[(g * S + s) * W + f0_r + w], w < l_r (S = the chunk's steps, f0_r =
+// the node's first function record in processing order, W = F rounded up to
+// 4 words):
 //   w = 0:          lanes perturbed at this node (category 0)
 //   w = 1 .. l-1:   lanes that selected function w-1
 // The last function's lanes are the valid lanes in none of those words.
 // Global perturbation also stores, per (s, g), the OR of all nodes' w = 0
 // words in word F of the same run (W = F + 1 rounded up to 4): the chains
-// that take s XOR gamma.  A step's words of consecutive groups are one
-// contiguous, 16-byte aligned run, so one bulk copy moves a CTA's step.
+// that take s XOR gamma.  A group's words of consecutive steps are one
+// contiguous, 16-byte aligned run, so one bulk copy moves several steps of a
+// group.
 //
 // Both kernels compare the same digits against the same bounds as the fused
 // kernel (draw_below), so the chains are bit-identical under either schedule.
@@ -81,8 +83,9 @@ __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Sim
   c.vmask = active ? lane_mask(a.omega, c.g) : 0u;
   c.t = a.t0 + (uint64_t)s;
   c.sub = 0;
-  uint32_t *out = a.planes + sg * a.W + c.f0;
-  uint32_t *anyw = a.planes + sg * a.W + a.F;
+  const int64_t run = (int64_t)c.g * a.steps + s;  // group-major: a group's steps are contiguous
+  uint32_t *out = a.planes + run * a.W + c.f0;
+  uint32_t *anyw = a.planes + run * a.W + a.F;
   switch ((int)__reduce_max_sync(kFull, (unsigned)c.L)) {
     case 0: break;
     case 1: select_item<1, MODE, BPR>(a.rk, a.P32, c, out, anyw); break;
@@ -259,13 +262,17 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
   }
   for (int j = threadIdx.x; j < max(a.n_props, 1) * gpb * kIndRing; j += blockDim.x) ind[j] = kFull;
   __syncthreads();  // tables and state staged before any thread reads another's records
-  // step s's words of this CTA's groups: one contiguous run of ngl * W words
-  const int chunks16 = ngl * W / 4;
+  // step s's words of this CTA's groups: ngl runs of W words (group-major
+  // layout), copied 16 bytes at a time into slot s % kRing
+  const int w16 = W / 4, chunks16 = ngl * w16;
+  auto chunk_src = [&](int s, int j) {
+    const int gl = j / w16;
+    return a.planes + ((size_t)(g0 + gl) * a.steps + s) * W + 4 * (j - gl * w16);
+  };
   auto issue = [&](int s) {
     if (s < a.steps) {
-      const uint32_t *src = a.planes + ((size_t)s * a.G + g0) * W;
       uint32_t *dst = ring + (size_t)(s % kRing) * gpb * W;
-      for (int j = threadIdx.x; j < chunks16; j += blockDim.x) copy16_async(dst + 4 * j, src + 4 * j);
+      for (int j = threadIdx.x; j < chunks16; j += blockDim.x) copy16_async(dst + 4 * j, chunk_src(s, j));
     }
     async_commit();  // one group per step, empty past the end, so the wait count stays uniform
   };
@@ -371,9 +378,8 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
     }
     auto issue_warp = [&](int s) {
       if (s < a.steps) {
-        const uint32_t *src = a.planes + ((size_t)s * a.G + g0) * W;
         uint32_t *dst = ring + (size_t)(s % kRing) * slot_words;
-        for (int j = lane; j < chunks16; j += 32) copy16_async(dst + 4 * j, src + 4 * j);
+        for (int j = lane; j < chunks16; j += 32) copy16_async(dst + 4 * j, chunk_src(s, j));
       }
       async_commit();
     };
@@ -502,12 +508,15 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
 // scheduler two or more warps of equal work, so the dependent levels of one
 // warp's trees overlap with another's.
 //
-// Feeding: the category words of one step for the CTA's groups are one
-// contiguous run, so one thread of the last warp (the producer) moves a step
-// with one bulk copy (cp.async.bulk) into a ring slot, completing the slot's
-// mbarrier.  Between the barriers of steps s-1 and s it refills the slot that
-// step s-1 used and waits for the words of step s+1, so the barrier that ends
-// step s also publishes them; the item threads never wait on an mbarrier.
+// Feeding: a group's category words of kCopySteps consecutive steps are one
+// contiguous run (group-major layout), so one thread of the last warp (the
+// producer) moves a chunk of 4 steps with one bulk copy (cp.async.bulk) per
+// group of the CTA into a ring slot, completing the slot's mbarrier.  At the
+// first step of chunk c it refills the slot chunk c-1 used; at the last step
+// of chunk c it waits for chunk c+1's words, so the barrier that ends that
+// step also publishes them.  Copy and wait, whose latency the barrier of that
+// step pays, come once per 4 steps; the item threads never wait on an
+// mbarrier.
 // The wait is bounded (1 s): if it gives up, the producer records
 // PBN_ERR_TIMEOUT in the device status word, issues nothing more and lets the
 // launch run to its end (the results are then invalid and the status says
@@ -520,6 +529,7 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
 namespace {
 
 constexpr int kResStride = 512;  // words between the two state buffers
+constexpr int kCopySteps = 4;    // steps of category words per bulk copy
 
 __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
   uint32_t v;
@@ -578,8 +588,15 @@ __device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity) {
   return mbar_try(bar, parity) || mbar_wait_slow(bar, parity);
 }
 
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+// The slot's mbarrier expects `bytes` from the copies that follow (this
+// arrival completes the phase once they have landed).
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// One bulk copy global -> shared (16-byte aligned, size a multiple of 16)
+// completing its bytes on the mbarrier.
+__device__ __forceinline__ void bulk_copy_to(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
@@ -679,10 +696,11 @@ __device__ __forceinline__ uint32_t rest_part(uint32_t w, int L, int LW, int f, 
 
 }  // namespace
 
+// ring: steps in flight (8 or 16), in slots of kCopySteps steps each
 size_t apply_resident_smem_bytes(int gpb, int W, int ring, int n_props) {
   size_t b = (size_t)2 * kResStride * 4;                     // state buffers
   b += (size_t)ring * gpb * W * 4;                           // category words ring (16-byte slots)
-  b += (size_t)ring * 8;                                     // one mbarrier per slot
+  b += (size_t)(ring / kCopySteps) * 8;                      // one mbarrier per slot
   b += (size_t)std::max(n_props, 1) * gpb * kIndRing * 4;    // indicator words of recent steps
   return b;
 }
@@ -695,12 +713,13 @@ __global__ void __launch_bounds__(2 * kResidentItems + 32, 1) apply_resident_ker
   const int gpb = a.gpb, n = a.n, W = a.W;
   const uint32_t g0 = blockIdx.x * (uint32_t)gpb;
   const int ngl = min(gpb, a.G - (int)g0);
-  const int ring = 1 << a.ring_log2, rmask = ring - 1, rlog = a.ring_log2;
-  const int slot_words = gpb * W;
+  constexpr int K = kCopySteps;
+  const int nslot = (1 << a.ring_log2) / K, smask = nslot - 1, slog = a.ring_log2 - 2;  // K = 4 = 2^2
+  const int slot_words = gpb * K * W;                          // [gl][K steps][W]
   uint32_t *st = reinterpret_cast<uint32_t *>(smem);          // [2][kResStride]
-  uint32_t *ringp = st + 2 * kResStride;                      // [ring][slot_words]
-  uint64_t *full = reinterpret_cast<uint64_t *>(ringp + (size_t)ring * slot_words);
-  uint32_t *ind = reinterpret_cast<uint32_t *>(full + ring);  // [n_props][gpb][kIndRing]
+  uint32_t *ringp = st + 2 * kResStride;                      // [nslot][slot_words]
+  uint64_t *full = reinterpret_cast<uint64_t *>(ringp + (size_t)nslot * slot_words);
+  uint32_t *ind = reinterpret_cast<uint32_t *>(full + nslot);  // [n_props][gpb][kIndRing]
   const int n_ind = max(a.n_props, 1) * gpb * kIndRing;
   const int items = n * gpb;
   for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
@@ -712,31 +731,37 @@ __global__ void __launch_bounds__(2 * kResidentItems + 32, 1) apply_resident_ker
   const bool producer = warp == (int)(blockDim.x >> 5) - 1;
   const uint32_t full0 = smem_u32(full), ring0 = smem_u32(ringp);
   const uint32_t slot_bytes = (uint32_t)slot_words * 4u;
-  const uint32_t copy_bytes = (uint32_t)(ngl * W) * 4u;
+  const int nchunks = (a.steps + K - 1) / K;  // copies of K steps (the last may be shorter)
   if (threadIdx.x == 0) {
-    for (int j = 0; j < ring; j++) mbar_init(full + j);
+    for (int j = 0; j < nslot; j++) mbar_init(full + j);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   cta_barrier();  // tables, state and barriers ready
   if (producer) {
-    // thread 0 of the warp: copies issued (steps 0 .. issued-1) and confirmed
-    // (0 .. waited-1); `dead` once a wait gave up
+    // thread 0 of the warp: chunks of K steps issued (0 .. issued-1) and
+    // confirmed (0 .. waited-1); `dead` once a wait gave up.  Chunk c is one
+    // bulk copy per group of the CTA into slot c % nslot, all completing the
+    // slot's mbarrier.
     int issued = 0, waited = 0;
     bool dead = false;
-    auto issue = [&](int s) {
-      const int slot = s & rmask;
-      bulk_copy(ring0 + (uint32_t)slot * slot_bytes, a.planes + ((size_t)s * a.G + g0) * W, copy_bytes,
-                full0 + 8u * slot);
-      issued = s + 1;
+    auto issue = [&](int c) {
+      const int slot = c & smask;
+      const int kc = min(K, a.steps - c * K);
+      const uint32_t bar = full0 + 8u * slot, bytes = (uint32_t)(kc * W) * 4u;
+      mbar_expect_tx(bar, bytes * (uint32_t)ngl);
+      for (int gl = 0; gl < ngl; gl++)
+        bulk_copy_to(ring0 + (uint32_t)slot * slot_bytes + (uint32_t)(gl * K * W) * 4u,
+                     a.planes + ((size_t)(g0 + gl) * a.steps + (size_t)c * K) * W, bytes, bar);
+      issued = c + 1;
     };
-    auto wait_step = [&](int s) {
+    auto wait_chunk = [&](int c) {
       if (dead) return;
-      if (!mbar_wait_fast(full0 + 8u * (s & rmask), (uint32_t)((s >> rlog) & 1))) {
+      if (!mbar_wait_fast(full0 + 8u * (c & smask), (uint32_t)((c >> slog) & 1))) {
         atomicExch(a.status, PBN_ERR_TIMEOUT);
         dead = true;
         return;
       }
-      waited = s + 1;
+      waited = c + 1;
     };
     // the warp stores the indicator words of steps s0 .. s0+cnt-1 (complete)
     // and makes their ring words ready for reuse
@@ -755,15 +780,18 @@ __global__ void __launch_bounds__(2 * kResidentItems + 32, 1) apply_resident_ker
         }
     };
     if (lane == 0) {
-      for (int s = 0; s < min(ring, a.steps); s++)
-        if (!(a.test_stall && s == 0)) issue(s);  // test hook: step 0's words never arrive
-      wait_step(0);
+      for (int c = 0; c < min(nslot, nchunks); c++)
+        if (!(a.test_stall && c == 0)) issue(c);  // test hook: the first chunk never arrives
+      wait_chunk(0);
     }
-    cta_barrier();  // the words of step 0 landed
+    cta_barrier();  // the words of chunk 0 landed
     for (int s = 0; s < a.steps; s++) {
       if (lane == 0) {
-        if (s >= 1 && !dead && s - 1 + ring < a.steps) issue(s - 1 + ring);  // the slot step s-1 used
-        if (s + 1 < a.steps) wait_step(s + 1);
+        const int c = s / K;
+        // first step of chunk c: refill the slot chunk c-1 used (its steps are done)
+        if (s % K == 0 && c >= 1 && !dead && c - 1 + nslot < nchunks) issue(c - 1 + nslot);
+        // last step of chunk c: the words of chunk c+1 must land before this step's barrier
+        if (s % K == K - 1 && c + 1 < nchunks) wait_chunk(c + 1);
       }
       __syncwarp();
       if (s > 0 && (s & 31) == 0) flush(s - 32, 32);  // steps s-32 .. s-1 are complete
@@ -773,8 +801,8 @@ __global__ void __launch_bounds__(2 * kResidentItems + 32, 1) apply_resident_ker
     flush(done, a.steps - done);
     // every issued copy has landed before the CTA's shared memory goes away
     if (lane == 0)
-      for (int s = waited; s < issued; s++)
-        if (!mbar_wait_fast(full0 + 8u * (s & rmask), (uint32_t)((s >> rlog) & 1))) {
+      for (int c = waited; c < issued; c++)
+        if (!mbar_wait_fast(full0 + 8u * (c & smask), (uint32_t)((c >> slog) & 1))) {
           atomicExch(a.status, PBN_ERR_TIMEOUT);
           break;
         }
@@ -791,8 +819,10 @@ __global__ void __launch_bounds__(2 * kResidentItems + 32, 1) apply_resident_ker
   const uint32_t vmask = active ? lane_mask(a.omega, g0 + gl) : 0u;
   const uint32_t st0 = smem_u32(st);
   const uint32_t own = st0 + 4u * (uint32_t)(active ? idx : 0);
-  const uint32_t woff = active ? 4u * (uint32_t)(gl * W + f0) : 0u;  // the item's words within a slot
-  const uint32_t aoff = active ? 4u * (uint32_t)(gl * W + a.F) : 0u; // the group's OR of perturbed lanes
+  // the item's words of step s: ring0 + (s/K % nslot) slot_bytes + (s % K) W + woff (bytes: x 4)
+  const uint32_t woff = active ? 4u * (uint32_t)(gl * K * W + f0) : 0u;
+  const uint32_t aoff = active ? 4u * (uint32_t)(gl * K * W + a.F) : 0u;  // the group's OR of perturbed lanes
+  const uint32_t step_bytes = 4u * (uint32_t)W;
   const bool writer = active && f == 0;
   ResidentFn R;
   if (f < L) R.load(a.fn[f0 + f], st0, gpb, gl);
@@ -817,7 +847,8 @@ __global__ void __launch_bounds__(2 * kResidentItems + 32, 1) apply_resident_ker
     constexpr int CUR = decltype(cur_tag)::value;
     constexpr int OFF_CUR = CUR * kResStride * 4, OFF_NXT = (1 - CUR) * kResStride * 4;
     {
-      const uint32_t w = ring0 + (uint32_t)(s & rmask) * slot_bytes + woff;
+      const uint32_t sb = ring0 + (uint32_t)((s / K) & smask) * slot_bytes + (uint32_t)(s % K) * step_bytes;
+      const uint32_t w = sb + woff;
       const uint32_t P = lds_u32(w);
       const uint32_t S1 = L > 1 ? lds_u32(w + 4u) : 0u;  // lanes of function 0 (L > 1)
       const uint32_t old = writer ? lds_u32_at<OFF_CUR>(own) : 0u;
@@ -836,7 +867,7 @@ __global__ void __launch_bounds__(2 * kResidentItems + 32, 1) apply_resident_ker
       if (MODE == PBN_PERTURB_PER_NODE) {
         nv = (P & ~old) | fword;
       } else {
-        const uint32_t any = lds_u32(ring0 + (uint32_t)(s & rmask) * slot_bytes + aoff);
+        const uint32_t any = lds_u32(sb + aoff);
         nv = (any & (old ^ P)) | (~any & fword);
       }
       if (writer) sts_u32_at<OFF_NXT>(own, nv);
@@ -873,7 +904,7 @@ cudaError_t launch_apply_resident(const SimArgs &a, int mode, bool rest, int thr
   const int blocks = (a.G + a.gpb - 1) / a.gpb;
   if (blocks == 0 || a.steps == 0) return cudaSuccess;
   if (threads % 32 || threads < 64 || threads > 2 * kResidentItems + 32 || 2 * a.n * a.gpb > threads - 32 ||
-      a.ring_log2 < 2 || a.ring_log2 > 4 || a.has_wide)
+      a.ring_log2 < 3 || a.ring_log2 > 4 || a.has_wide)
     return cudaErrorInvalidValue;
   if (mode == PBN_PERTURB_PER_NODE)
     return rest ? launch_resident_mode<PBN_PERTURB_PER_NODE, true>(a, blocks, threads, smem, s)
