@@ -427,12 +427,12 @@ def run_ours(args):
         other = {}
     achieved = ops_per_group_step * groups_steps / (k_ms / 1e3) / 1e12
     # DRAM bytes per launch of the dominant kernel, from the ncu capture of
-    # apply_resident_kernel on this workload (256 steps x 32 groups: 6596864
-    # bytes read, 0 written; cold caches, as ncu replays a launch): 805 bytes
+    # apply_resident_kernel on this workload (256 steps x 32 groups: 6599680
+    # bytes read, 0 written; cold caches, as ncu replays a launch): 806 bytes
     # per (group, step), the category words, scaled to the average launch
     traffic = None
     if apply_launches:
-        traffic = 6596864.0 / (256 * 32) * groups_steps / max(apply_launches, 1)
+        traffic = 6599680.0 / (256 * 32) * groups_steps / max(apply_launches, 1)
     lat = sorted(times)
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

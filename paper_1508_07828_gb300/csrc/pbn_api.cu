@@ -349,7 +349,7 @@ int plan_select(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, in
   const int pair_threads = (2 * items + 31) / 32 * 32;
   if (T == 1 && !net.has_wide && items <= pbn::kResidentItems &&
       (threads_req == 0 || threads_req == pair_threads + 32)) {
-    for (int lg = 4; lg >= 3; lg--) {  // 16 or 8 steps in flight, 4 per copy
+    for (int lg = 4; lg >= 4; lg--) {  // 16 steps in flight, 8 per copy (measured: 32 gains nothing)
       const size_t b = pbn::apply_resident_smem_bytes(gpb, W, 1 << lg, n_props);
       if ((int64_t)b <= maxs) {
         p->resident = true;

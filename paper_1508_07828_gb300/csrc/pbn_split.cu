@@ -510,13 +510,13 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
 //
 // Feeding: a group's category words of kCopySteps consecutive steps are one
 // contiguous run (group-major layout), so one thread of the last warp (the
-// producer) moves a chunk of 4 steps with one bulk copy (cp.async.bulk) per
-// group of the CTA into a ring slot, completing the slot's mbarrier.  At the
-// first step of chunk c it refills the slot chunk c-1 used; at the last step
-// of chunk c it waits for chunk c+1's words, so the barrier that ends that
-// step also publishes them.  Copy and wait, whose latency the barrier of that
-// step pays, come once per 4 steps; the item threads never wait on an
-// mbarrier.
+// producer) moves a chunk of kCopySteps = 8 steps with one bulk copy
+// (cp.async.bulk) per group of the CTA into a ring slot, completing the slot's
+// mbarrier.  At the first step of chunk c it refills the slot chunk c-1 used;
+// at the last step of chunk c it waits for chunk c+1's words, so the barrier
+// that ends that step also publishes them.  Copy and wait, whose latency the
+// barrier of that step pays, come once per 8 steps; the item threads never
+// wait on an mbarrier.
 // The wait is bounded (1 s): if it gives up, the producer records
 // PBN_ERR_TIMEOUT in the device status word, issues nothing more and lets the
 // launch run to its end (the results are then invalid and the status says
@@ -529,7 +529,9 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
 namespace {
 
 constexpr int kResStride = 512;  // words between the two state buffers
-constexpr int kCopySteps = 4;    // steps of category words per bulk copy
+constexpr int kCopyLog = 3;                 // log2 of the steps of category words per bulk copy
+constexpr int kCopySteps = 1 << kCopyLog;
+constexpr int kRingLogMax = 4;              // at most 16 steps in flight
 
 __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
   uint32_t v;
@@ -696,7 +698,7 @@ __device__ __forceinline__ uint32_t rest_part(uint32_t w, int L, int LW, int f, 
 
 }  // namespace
 
-// ring: steps in flight (8 or 16), in slots of kCopySteps steps each
+// ring: steps in flight (16), in slots of kCopySteps steps each
 size_t apply_resident_smem_bytes(int gpb, int W, int ring, int n_props) {
   size_t b = (size_t)2 * kResStride * 4;                     // state buffers
   b += (size_t)ring * gpb * W * 4;                           // category words ring (16-byte slots)
@@ -714,7 +716,7 @@ __global__ void __launch_bounds__(2 * kResidentItems + 32, 1) apply_resident_ker
   const uint32_t g0 = blockIdx.x * (uint32_t)gpb;
   const int ngl = min(gpb, a.G - (int)g0);
   constexpr int K = kCopySteps;
-  const int nslot = (1 << a.ring_log2) / K, smask = nslot - 1, slog = a.ring_log2 - 2;  // K = 4 = 2^2
+  const int nslot = (1 << a.ring_log2) / K, smask = nslot - 1, slog = a.ring_log2 - kCopyLog;
   const int slot_words = gpb * K * W;                          // [gl][K steps][W]
   uint32_t *st = reinterpret_cast<uint32_t *>(smem);          // [2][kResStride]
   uint32_t *ringp = st + 2 * kResStride;                      // [nslot][slot_words]
@@ -904,7 +906,7 @@ cudaError_t launch_apply_resident(const SimArgs &a, int mode, bool rest, int thr
   const int blocks = (a.G + a.gpb - 1) / a.gpb;
   if (blocks == 0 || a.steps == 0) return cudaSuccess;
   if (threads % 32 || threads < 64 || threads > 2 * kResidentItems + 32 || 2 * a.n * a.gpb > threads - 32 ||
-      a.ring_log2 < 3 || a.ring_log2 > 4 || a.has_wide)
+      a.ring_log2 < kCopyLog + 1 || a.ring_log2 > kRingLogMax || a.has_wide)
     return cudaErrorInvalidValue;
   if (mode == PBN_PERTURB_PER_NODE)
     return rest ? launch_resident_mode<PBN_PERTURB_PER_NODE, true>(a, blocks, threads, smem, s)
