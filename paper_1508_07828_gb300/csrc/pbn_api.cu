@@ -156,8 +156,10 @@ int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, in
   return PBN_OK;
 }
 
+// status: the device status word the kernels' bounded waits report to (the
+// device's own word unless a caller such as the engine keeps one)
 pbn::SimArgs make_args(const pbn::NetDev &net, const pbn_run_cfg &cfg, const pbn_chains &ch, int64_t steps,
-                       const LaunchPlan &plan) {
+                       const LaunchPlan &plan, int *status = nullptr) {
   pbn::SimArgs a;
   memset(&a, 0, sizeof a);
   a.rk = pbn::make_round_keys(cfg.seed);
@@ -182,7 +184,7 @@ pbn::SimArgs make_args(const pbn::NetDev &net, const pbn_run_cfg &cfg, const pbn
   a.wide_tt = net.d_wide_tt;
   a.wide_par = net.d_wide_par;
   a.has_wide = net.has_wide;
-  a.status = pbn::device_status();
+  a.status = status ? status : pbn::device_status();
   {
     static const int stall = getenv("PBN_TEST_STALL_FIRST_TILE") ? atoi(getenv("PBN_TEST_STALL_FIRST_TILE")) : 0;
     a.test_stall = stall;
@@ -373,7 +375,8 @@ struct ApplyTiming {
 };
 
 int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, bool record,
-                     const SelectPlan &sp, cudaStream_t s, int64_t *launches, ApplyTiming *timing) {
+                     const SelectPlan &sp, cudaStream_t s, int64_t *launches, ApplyTiming *timing,
+                     int *status = nullptr) {
   const int G = (int)((ch.omega + 31) / 32);
   const int64_t per_step = (int64_t)G * sp.W * 4;
   const int64_t C = std::max<int64_t>(1, std::min(kSelectMaxSteps, kSelectBudgetBytes / per_step));
@@ -434,7 +437,7 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
     if (pipe && i >= 3 && steps - done <= C) k = steps - done;
     const int b = pipe ? (int)(i & 1) : 0;
     cudaStream_t ss = pipe ? sc->side : s;
-    pbn::SimArgs a = make_args(net, cfg, ch, k, lp);
+    pbn::SimArgs a = make_args(net, cfg, ch, k, lp, status);
     if (!record) a.soi_size = 0;
     a.W = sp.W;
     a.planes = sc->planes[b];
@@ -473,7 +476,7 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
 }
 
 int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, cudaStream_t s,
-              int64_t *launches = nullptr, ApplyTiming *timing = nullptr) {
+              int64_t *launches = nullptr, ApplyTiming *timing = nullptr, int *status = nullptr) {
   if (steps < 0) return fail(PBN_ERR_INVALID, "negative step count");
   if (steps == 0) return PBN_OK;
   const bool record = ch.bits && ch.bits_cap > 0 && n_recorded_props(cfg) > 0;
@@ -500,7 +503,7 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
     const std::string saved = g_err;
     int rc = plan_select(net, ch.omega, cfg.perturb_mode, cfg.groups_per_block, cfg.threads_per_block,
                          cfg.threads_per_item, cfg.staging, n_recorded_props(cfg), &sp);
-    if (rc == PBN_OK) return run_select_ahead(net, cfg, ch, steps, record, sp, s, launches, timing);
+    if (rc == PBN_OK) return run_select_ahead(net, cfg, ch, steps, record, sp, s, launches, timing, status);
     if (cfg.schedule == PBN_SCHEDULE_SELECT_AHEAD) return rc;
     g_err = saved;  // automatic choice: fall back to the fused schedule
   }
@@ -511,7 +514,7 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
   const int64_t chunk = 1 << 30;
   for (int64_t done = 0; done < steps; done += chunk) {
     const int64_t k = std::min(chunk, steps - done);
-    pbn::SimArgs a = make_args(net, cfg, ch, k, plan);
+    pbn::SimArgs a = make_args(net, cfg, ch, k, plan, status);
     if (!record) a.soi_size = 0;
     CUDA_TRY(pbn::launch_sim(a, cfg.perturb_mode, plan.T, plan.BPR, plan.threads, plan.smem, s),
              "simulation launch");
@@ -524,6 +527,14 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
 }  // namespace
 
 void pbn::set_last_error(const char *msg) { g_err = msg; }
+
+// One query's extension outside the batched kernel (the engine's epochs with
+// a single small query): the schedule pbn_run_chains would pick, the bounded
+// waits reporting to `status`.
+int pbn::run_chains_alone(const NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, cudaStream_t s,
+                          int *status, int64_t *launches) {
+  return run_steps(net, cfg, ch, steps, s, launches, nullptr, status);
+}
 
 namespace {
 // Reads and clears the device status word (synchronous).

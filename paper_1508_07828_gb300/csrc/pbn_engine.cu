@@ -875,20 +875,47 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       }
     }
   }
+  ECUDA(cudaEventRecord(e->e0, e->s), "event");
+  // A lone query with few chain groups, nothing waiting for admission: the
+  // batched fused kernel would leave most SMs idle and wait on its Philox
+  // rounds every step, so its extension runs alone with the schedule
+  // pbn_run_chains picks (the same chains, bit for bit); the statistics stay
+  // in the batched launch.  Not a tuning sample.
+  bool alone = false;
+  if (ntask == 1 && e->pending.empty()) {
+    EQuery &q = *e->epoch_queries[0];
+    if (2 * q.G <= e->sms && q.sim_D > 0) {
+      pbn_run_cfg rc_cfg;
+      memset(&rc_cfg, 0, sizeof rc_cfg);
+      rc_cfg.seed = q.seed;
+      rc_cfg.perturb_mode = q.mode;
+      rc_cfg.soi.size = (int32_t)q.soi_nodes.size();
+      rc_cfg.soi.nodes = q.soi_nodes.data();
+      rc_cfg.soi.values = q.soi_vals.data();
+      pbn_chains c = q.ch;  // q.ch.length advances when the epoch is applied
+      int64_t l = 0;
+      if (run_chains_alone(q.dev(), rc_cfg, c, q.sim_D, e->s, e->status, &l) == PBN_OK) {
+        alone = true;
+        nitems = 0;
+        launches += (int)l;
+      } else {
+        set_last_error("");  // fall back to the batched kernel
+      }
+    }
+  }
   e->h_cnt[0] = nitems;
   e->h_cnt[1] = 0;
   e->h_cnt[2] = vblocks;
   e->h_cnt[3] = 0;
   e->h_cnt[4] = nreq;
-  ECUDA(cudaEventRecord(e->e0, e->s), "event");
   if (nitems || nreq) {
     if (e->cfg.use_graph) {
       if ((rc = capture_graph(e, cand.threads, smem))) return rc;
       ECUDA(cudaGraphLaunch(e->exec, e->s), "graph launch");
-      launches = 2;
+      launches += 2;
     } else {
       if ((rc = launch_direct(e, cand.threads, smem, ntask, nitems, nreq))) return rc;
-      launches = (nitems ? 1 : 0) + (nreq ? 1 : 0);
+      launches += (nitems ? 1 : 0) + (nreq ? 1 : 0);
     }
   }
   ECUDA(cudaEventRecord(e->e1, e->s), "event");
@@ -927,7 +954,7 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       launches += 2;
     }
   }
-  if (e->best < 0 && updates > 0) {
+  if (e->best < 0 && updates > 0 && !alone) {
     Candidate &c = e->cands[ci];
     c.ms += ms;
     c.updates += updates;

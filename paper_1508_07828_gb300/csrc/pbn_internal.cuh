@@ -120,6 +120,12 @@ struct SimArgs {
 };
 static_assert(sizeof(SimArgs) % 4 == 0, "SimArgs is copied word by word");
 
+// One extension of a chain set by the schedule pbn_run_chains picks, its
+// bounded waits reporting to `status` (pbn_api.cu; the engine's epochs with a
+// single small query).  Advances ch.length; adds its launches to *launches.
+int run_chains_alone(const NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, cudaStream_t s,
+                     int *status, int64_t *launches);
+
 // Sets the thread-local message returned by pbn_last_error (pbn_api.cu).
 void set_last_error(const char *msg);
 
