@@ -280,8 +280,9 @@ int ensure_side(SelectScratch *sc) {
 }
 
 struct SelectPlan {
-  int gpb, threads, staging, W, ring, T;
-  bool resident;  // apply_resident_kernel (one thread per item, `ring` slots of bulk copies)
+  int gpb, threads, staging, W, T;
+  int ring;       // one-thread apply: ring slots; resident apply: log2 of the ring's steps
+  bool resident;  // apply_resident_kernel (two threads per item, bulk-copied steps)
   size_t smem;
 };
 
@@ -345,22 +346,21 @@ int plan_select(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, in
   p->resident = false;
   // One thread per item asked for, every item resident for the whole launch:
   // the register-resident kernel (two threads per item, one per function
-  // slot) with a ring of bulk-copied steps, 16 slots or fewer when shared
-  // memory is short; staging requests other than tiles read the records
-  // beyond a node's second from global memory there.
+  // slot) with a ring of 16 bulk-copied steps (two copies of 8 in flight;
+  // measured: 32 steps gain nothing).  When the ring does not fit in shared
+  // memory the one-thread apply runs instead.  Staging requests other than
+  // tiles read the records beyond a node's second from global memory there.
   const int pair_threads = (2 * items + 31) / 32 * 32;
   if (T == 1 && !net.has_wide && items <= pbn::kResidentItems &&
       (threads_req == 0 || threads_req == pair_threads + 32)) {
-    for (int lg = 4; lg >= 4; lg--) {  // 16 steps in flight, 8 per copy (measured: 32 gains nothing)
-      const size_t b = pbn::apply_resident_smem_bytes(gpb, W, 1 << lg, n_props);
-      if ((int64_t)b <= maxs) {
-        p->resident = true;
-        p->ring = lg;
-        p->staging = pbn::STAGE_GLOBAL;
-        p->smem = b;
-        p->threads = pair_threads + 32;
-        break;
-      }
+    const int lg = 4;
+    const size_t b = pbn::apply_resident_smem_bytes(gpb, W, 1 << lg, n_props);
+    if ((int64_t)b <= maxs) {
+      p->resident = true;
+      p->ring = lg;
+      p->staging = pbn::STAGE_GLOBAL;
+      p->smem = b;
+      p->threads = pair_threads + 32;
     }
   }
   return PBN_OK;
