@@ -148,7 +148,10 @@ typedef struct pbn_run_cfg {
  * the library, grown on demand).  AUTO: select-ahead when the chain groups
  * (ceil(omega / 32)) number at most the SMs, the network has at most 1000
  * nodes or the groups at most half the SMs, and its shared memory fits; else
- * fused. */
+ * fused.  FUSED with more groups than SMs, not a whole multiple of them, an
+ * automatic groups_per_block and at least 64 steps: two launches, the first
+ * running the SMs that carry one group more for fewer steps, the second
+ * finishing those groups spread over all SMs (same chains). */
 enum { PBN_SCHEDULE_AUTO = 0, PBN_SCHEDULE_FUSED = 1, PBN_SCHEDULE_SELECT_AHEAD = 2 };
 
 /* ---------------------------------------------------------------- network */

@@ -475,6 +475,44 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
   return PBN_OK;
 }
 
+// Balanced fused launches for G chain groups over R CTAs (one per SM), when
+// G / R is not whole: with q = G / R and rem = G % R, one launch makes every SM
+// carry q + 1 groups for all k steps, time (q+1) k.  Instead, phase 1 gives
+// R - rem CTAs q groups for k steps and rem CTAs q + 1 groups for
+// x = k q / (q+1) steps (both about q k); phase 2 spreads the rem (q+1)
+// lagging groups over the R CTAs for their last k - x steps.  Every group
+// still takes its own transitions in order, so the chains are the same.
+// Returns false (one launch) when this does not save time.
+bool balance_phases(int G, int R, int gpb, int64_t k, pbn::SimArgs *ph1, pbn::SimArgs *ph2) {
+  if (R <= 0 || G <= R || k < 64) return false;
+  const int q = G / R, rem = G % R;
+  if (rem == 0 || gpb < q + 1) return false;
+  const int lag = rem * (q + 1);
+  const int b2 = std::min(R, lag);
+  const int per2 = (lag + b2 - 1) / b2;
+  const int64_t x = k * q / (q + 1);
+  // phase 1 about q k, phase 2 about per2 k / (q+1), against (q+1) k
+  if ((int64_t)q * (q + 1) + per2 >= (int64_t)(q + 1) * (q + 1)) return false;
+  ph1->seg_blocks[0] = R - rem;
+  ph1->seg_g0[0] = 0;
+  ph1->seg_ng[0] = (R - rem) * q;
+  ph1->seg_steps[0] = (int)k;
+  ph1->seg_soff[0] = 0;
+  ph1->seg_blocks[1] = rem;
+  ph1->seg_g0[1] = (R - rem) * q;
+  ph1->seg_ng[1] = lag;
+  ph1->seg_steps[1] = (int)x;
+  ph1->seg_soff[1] = 0;
+  ph2->seg_blocks[0] = b2;
+  ph2->seg_g0[0] = (R - rem) * q;
+  ph2->seg_ng[0] = lag;
+  ph2->seg_steps[0] = (int)(k - x);
+  ph2->seg_soff[0] = (int)x;
+  ph2->seg_blocks[1] = 0;
+  ph2->seg_g0[1] = ph2->seg_ng[1] = ph2->seg_steps[1] = ph2->seg_soff[1] = 0;
+  return true;
+}
+
 int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, int64_t steps, cudaStream_t s,
               int64_t *launches = nullptr, ApplyTiming *timing = nullptr, int *status = nullptr) {
   if (steps < 0) return fail(PBN_ERR_INVALID, "negative step count");
@@ -516,10 +554,20 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
     const int64_t k = std::min(chunk, steps - done);
     pbn::SimArgs a = make_args(net, cfg, ch, k, plan, status);
     if (!record) a.soi_size = 0;
-    CUDA_TRY(pbn::launch_sim(a, cfg.perturb_mode, plan.T, plan.BPR, plan.threads, plan.smem, s),
-             "simulation launch");
+    pbn::SimArgs a2 = a;
+    // automatic shape only: a requested groups_per_block keeps its one launch
+    if (cfg.groups_per_block == 0 && balance_phases(a.G, sm_count(), plan.gpb, k, &a, &a2)) {
+      CUDA_TRY(pbn::launch_sim(a, cfg.perturb_mode, plan.T, plan.BPR, plan.threads, plan.smem, s),
+               "simulation launch");
+      CUDA_TRY(pbn::launch_sim(a2, cfg.perturb_mode, plan.T, plan.BPR, plan.threads, plan.smem, s),
+               "simulation launch");
+      if (launches) *launches += 2;
+    } else {
+      CUDA_TRY(pbn::launch_sim(a, cfg.perturb_mode, plan.T, plan.BPR, plan.threads, plan.smem, s),
+               "simulation launch");
+      if (launches) *launches += 1;
+    }
     ch.length += k;
-    if (launches) *launches += 1;
   }
   return PBN_OK;
 }

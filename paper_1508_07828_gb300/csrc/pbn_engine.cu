@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(512) batch_sim_kernel(const SimArgs *__restric
     __syncthreads();
     const RoundKeys rk = s_task.rk;
     if (s_task.mode == PBN_PERTURB_PER_NODE)
-      cta_simulate<PBN_PERTURB_PER_NODE, 1, 1, true>(s_task, rk, (uint32_t)w.g0, w.ngl, smem);
+      cta_simulate<PBN_PERTURB_PER_NODE, 1, 1, true>(s_task, rk, (uint32_t)w.g0, w.ngl, s_task.gpb, smem, s_task.steps, 0);
     else
-      cta_simulate<PBN_PERTURB_GLOBAL, 1, 1, true>(s_task, rk, (uint32_t)w.g0, w.ngl, smem);
+      cta_simulate<PBN_PERTURB_GLOBAL, 1, 1, true>(s_task, rk, (uint32_t)w.g0, w.ngl, s_task.gpb, smem, s_task.steps, 0);
     __syncthreads();
   }
 }

@@ -116,6 +116,14 @@ struct SimArgs {
   int ring_log2;         // select-ahead, register-resident apply: log2 of the ring slots
   int n_props;           // properties recorded (entries soi_node[m] belong to property soi_prop[m])
   int64_t prop_stride;   // words between two properties' bitstreams (G * bits_cap)
+  // Fused kernel, balanced launch: CTAs 0 .. seg_blocks[0]-1 split groups
+  // seg_g0[0] .. seg_g0[0]+seg_ng[0]-1 evenly and advance them seg_steps[0]
+  // steps from transition t0 + seg_soff[0]; the next seg_blocks[1] CTAs do the
+  // same with segment 1.  seg_blocks[0] = 0: CTA b takes groups b*gpb ..
+  // b*gpb+gpb-1 for all `steps`.  gpb bounds the groups of any CTA.
+  int seg_blocks[2];
+  int seg_g0[2], seg_ng[2];
+  int seg_steps[2], seg_soff[2];
   uint8_t soi_prop[kMaxSoi];
 };
 static_assert(sizeof(SimArgs) % 4 == 0, "SimArgs is copied word by word");

@@ -1,10 +1,13 @@
 // Chain initialisation and the synchronous PBN step (Sec. 2.2) on sm_103a.
 //
 // Layout: bit-sliced chains.  One 32-bit word holds one node of 32 chains (a
-// chain group).  A CTA owns `gpb` groups and all n nodes of them: their
+// chain group).  A CTA owns up to `gpb` groups and all n nodes of them: their
 // current and next states sit in shared memory as [node][group] words, next
 // to the network tables.  An item is one (node, group) pair of one step:
-// 32 chain-node updates.  T threads share an item (T = 1, 2 or 4).
+// 32 chain-node updates.  T threads share an item (T = 1, 2 or 4).  A
+// balanced launch gives CTAs different group counts and step ranges (two
+// segments of SimArgs), so that two launches spread a group count that is not
+// a multiple of the SM count evenly over the SMs.
 //
 // Per item and transition t:
 //  1. Category of every lane's uniform u against the node's sorted bounds
@@ -38,8 +41,23 @@ namespace pbn {
 template <int MODE, int T, int BPR, bool WIDE>
 __global__ void __launch_bounds__(max_threads<T>()) sim_kernel(const __grid_constant__ SimArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const uint32_t g0 = blockIdx.x * (uint32_t)a.gpb;
-  cta_simulate<MODE, T, BPR, WIDE>(a, a.rk, g0, min(a.gpb, a.G - (int)g0), smem);
+  int g0 = (int)blockIdx.x * a.gpb, ngl = min(a.gpb, a.G - g0), nsteps = a.steps, soff = 0;
+  if (a.seg_blocks[0] != 0) {
+    // balanced launch: this CTA's share of its segment's groups
+    int b = (int)blockIdx.x, q = 0;
+    if (b >= a.seg_blocks[0]) {
+      b -= a.seg_blocks[0];
+      q = 1;
+    }
+    const int nb = a.seg_blocks[q];
+    const int lo = (int)((int64_t)b * a.seg_ng[q] / nb), hi = (int)((int64_t)(b + 1) * a.seg_ng[q] / nb);
+    g0 = a.seg_g0[q] + lo;
+    ngl = hi - lo;
+    nsteps = a.seg_steps[q];
+    soff = a.seg_soff[q];
+  }
+  // layout stride ngl: a CTA with fewer groups than a.gpb runs fewer item rounds
+  cta_simulate<MODE, T, BPR, WIDE>(a, a.rk, (uint32_t)g0, ngl, ngl, smem, nsteps, soff);
 }
 
 __global__ void init_kernel(const __grid_constant__ RoundKeys rk, uint32_t *state, int n, int G, int64_t omega) {
@@ -115,7 +133,7 @@ static cudaError_t launch_mode(const SimArgs &a, int T, int BPR, int blocks, int
 }
 
 cudaError_t launch_sim(const SimArgs &a, int mode, int T, int BPR, int threads, size_t smem, cudaStream_t s) {
-  const int blocks = (a.G + a.gpb - 1) / a.gpb;
+  const int blocks = a.seg_blocks[0] ? a.seg_blocks[0] + a.seg_blocks[1] : (a.G + a.gpb - 1) / a.gpb;
   if (blocks == 0 || a.steps == 0) return cudaSuccess;
   if (mode == PBN_PERTURB_PER_NODE) return launch_mode<PBN_PERTURB_PER_NODE>(a, T, BPR, blocks, threads, smem, s);
   return launch_mode<PBN_PERTURB_GLOBAL>(a, T, BPR, blocks, threads, smem, s);

@@ -309,16 +309,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: a 24 KB tile arrives in microseconds
 
-// One CTA's work: advance chain groups g0 .. g0+ngl-1 of task `a` by
-// a.steps transitions.  `rk` are the task's Philox round keys (kernel
-// parameters in the single-task kernel, registers in the batched one).
+// One CTA's work: advance chain groups g0 .. g0+ngl-1 of task `a` by nsteps
+// transitions, from transition a.t0 + soff (bitstream column a.col0 + soff).
+// `rk` are the task's Philox round keys (kernel parameters in the
+// single-task kernel, registers in the batched one).  The groups' words are
+// laid out [node][gpb] in shared memory, ngl <= gpb <= a.gpb.
 // Function records come from shared memory (whole tables), from TMA tiles
 // streamed through two shared buffers (tile u of the launch's sequence
 // s*ntiles + t goes to buffer u & 1), or straight from global memory.
 template <int MODE, int T, int BPR, bool WIDE>
-__device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &rk, uint32_t g0, int ngl,
-                                             unsigned char *smem) {
-  const int gpb = a.gpb;
+__device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &rk, uint32_t g0, int ngl, int gpb,
+                                             unsigned char *smem, int nsteps, int64_t soff) {
+  if (ngl <= 0) return;  // CTA-uniform
   const int n = a.n;
   const uint32_t P32 = a.P32;
   const int staging = a.staging;
@@ -361,7 +363,7 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
   if (MODE == PBN_PERTURB_GLOBAL)
     for (int j = threadIdx.x; j < 2 * gpb; j += blockDim.x) anyP[j] = 0u;
   const int ntiles = staging == STAGE_TILES ? a.ntiles : 1;
-  const int64_t total_tiles = (int64_t)a.steps * ntiles;
+  const int64_t total_tiles = (int64_t)nsteps * ntiles;
   if (staging == STAGE_TILES && threadIdx.x == 0) {
     mbar_init(&bar[0]);
     mbar_init(&bar[1]);
@@ -392,7 +394,7 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
   const int slot = threadIdx.x / T;
   const int nslots = blockDim.x / T;
   uint32_t *cur = bufA, *nxt = bufB;
-  for (int s = 0; s < a.steps; s++) {
+  for (int s = 0; s < nsteps; s++) {
     ItemCtx c;
     c.wide_tt = a.wide_tt;
     c.wide_par = a.wide_par;
@@ -402,7 +404,7 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
     c.pbuf = pbuf;
     c.anyP = anyP + (s & 1) * gpb;
     c.gpb = gpb;
-    c.t = a.t0 + (uint64_t)s;
+    c.t = a.t0 + (uint64_t)(soff + s);
     c.sub = sub;
     for (int t = 0; t < ntiles; t++) {
       int p0 = 0, p1 = n;
@@ -453,7 +455,7 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
       __syncthreads();
     }
     if (a.soi_size > 0) {
-      const int64_t col = a.col0 + s;
+      const int64_t col = a.col0 + soff + s;
       for (int gl = warp; gl < ngl; gl += nwarps) {
         uint32_t v = kFull;
         if (lane < a.soi_size) {
