@@ -477,22 +477,29 @@ int run_select_ahead(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains 
 
 // Balanced fused launches for G chain groups over R CTAs (one per SM), when
 // G / R is not whole: with q = G / R and rem = G % R, one launch makes every SM
-// carry q + 1 groups for all k steps, time (q+1) k.  Instead, phase 1 gives
-// R - rem CTAs q groups for k steps and rem CTAs q + 1 groups for
-// x = k q / (q+1) steps (both about q k); phase 2 spreads the rem (q+1)
-// lagging groups over the R CTAs for their last k - x steps.  Every group
-// still takes its own transitions in order, so the chains are the same.
-// Returns false (one launch) when this does not save time.
-bool balance_phases(int G, int R, int gpb, int64_t k, pbn::SimArgs *ph1, pbn::SimArgs *ph2) {
+// carry q + 1 groups for all k steps.  Instead, phase 1 gives R - rem CTAs q
+// groups for k steps and rem CTAs q + 1 groups for x < k steps, x chosen so
+// that both finish together; phase 2 spreads the rem (q+1) lagging groups
+// over the R CTAs for their last k - x steps.  Every group still takes its
+// own transitions in order, so the chains are the same.  Step cost of a CTA
+// with g groups: its item rounds ceil(n g T / threads) plus about 1.5 rounds
+// that do not scale with g (barrier, indicator, the last partial round);
+// measured on n = 2000, 1024 threads: 3 and 2 groups take 0.80 and 0.575 of
+// a 4-group step (the model: 0.79 and 0.58).  Returns false (one launch) when
+// the model saves nothing.
+bool balance_phases(int G, int R, const LaunchPlan &plan, int n, int64_t k, pbn::SimArgs *ph1,
+                    pbn::SimArgs *ph2) {
   if (R <= 0 || G <= R || k < 64) return false;
   const int q = G / R, rem = G % R;
-  if (rem == 0 || gpb < q + 1) return false;
+  if (rem == 0 || plan.gpb < q + 1) return false;
+  auto cost = [&](int g) {
+    return (double)(((int64_t)n * g * plan.T + plan.threads - 1) / plan.threads) + 1.5;
+  };
   const int lag = rem * (q + 1);
   const int b2 = std::min(R, lag);
   const int per2 = (lag + b2 - 1) / b2;
-  const int64_t x = k * q / (q + 1);
-  // phase 1 about q k, phase 2 about per2 k / (q+1), against (q+1) k
-  if ((int64_t)q * (q + 1) + per2 >= (int64_t)(q + 1) * (q + 1)) return false;
+  const int64_t x = std::min(k - 1, std::max<int64_t>(1, (int64_t)((double)k * cost(q) / cost(q + 1))));
+  if (cost(q) * (double)k + cost(per2) * (double)(k - x) >= cost(q + 1) * (double)k) return false;
   ph1->seg_blocks[0] = R - rem;
   ph1->seg_g0[0] = 0;
   ph1->seg_ng[0] = (R - rem) * q;
@@ -556,7 +563,7 @@ int run_steps(const pbn::NetDev &net, const pbn_run_cfg &cfg, pbn_chains &ch, in
     if (!record) a.soi_size = 0;
     pbn::SimArgs a2 = a;
     // automatic shape only: a requested groups_per_block keeps its one launch
-    if (cfg.groups_per_block == 0 && balance_phases(a.G, sm_count(), plan.gpb, k, &a, &a2)) {
+    if (cfg.groups_per_block == 0 && balance_phases(a.G, sm_count(), plan, net.n, k, &a, &a2)) {
       CUDA_TRY(pbn::launch_sim(a, cfg.perturb_mode, plan.T, plan.BPR, plan.threads, plan.smem, s),
                "simulation launch");
       CUDA_TRY(pbn::launch_sim(a2, cfg.perturb_mode, plan.T, plan.BPR, plan.threads, plan.smem, s),

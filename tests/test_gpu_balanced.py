@@ -42,23 +42,28 @@ def _run(P, net, soi, omega, seed, mode, chunks, **launch):
     return cs, states
 
 
-# (q, share of SMs that carry q + 1 groups, ragged chains in the last group)
-SHAPES = [(1, 3, 5), (3, None, 0), (2, 2, 17)]
+# (q, share of SMs that carry q + 1 groups, ragged chains in the last group,
+# nodes, threads per CTA).  One-warp CTAs make a group's items take more than
+# one round, so that q and q + 1 groups differ in step cost and the launch is
+# split; the default CTA of the 18-node network covers every item in one
+# round (one launch: nothing to balance).
+SHAPES = [(1, 3, 5, 18, 32), (3, None, 0, 18, 32), (2, 2, 17, 24, 32), (1, 3, 0, 18, 0)]
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("shape", SHAPES, ids=[f"q{s[0]}" for s in SHAPES])
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"q{s[0]}-n{s[3]}-t{s[4]}" for s in SHAPES])
 def test_balanced_launches_bit_exact(P, sms, shape, mode):
-    q, div, ragged = shape
+    q, div, ragged, n, threads = shape
     # q = 3 with 56 of 152 SMs one group over: the 16384-chain workload
     rem = (56 * sms) // 152 if div is None else sms // div
     G = _groups(sms, q, rem)
     omega = 32 * G - ragged
-    net = S.random_pbn(31 + q, 18, (1, 4), (1, 5), "biased", "powerlaw", 0.01)
+    net = S.random_pbn(31 + q, n, (1, 4), (1, 5), "biased", "powerlaw", 0.01)
     soi = S.StateOfInterest([0, 3, 7], [1, 0, 1])
     seed = 0xBA1 + q
     chunks = [64, 77]  # each call long enough to be split into two phases
-    cs, states = _run(P, net, soi, omega, seed, mode, chunks)
+    launch = dict(threads_per_block=threads) if threads else {}
+    cs, states = _run(P, net, soi, omega, seed, mode, chunks, **launch)
     ref = oracle.init_states(net, seed, omega)
     t0 = 0
     inds = []
@@ -70,7 +75,7 @@ def test_balanced_launches_bit_exact(P, sms, shape, mode):
     assert np.array_equal(cs.indicator_numpy(0, t0), np.concatenate(inds, axis=1))
     # the one-launch shape gives the same chains
     gpb = -(-G // sms)
-    one, s1 = _run(P, net, soi, omega, seed, mode, chunks, groups_per_block=gpb)
+    one, s1 = _run(P, net, soi, omega, seed, mode, chunks, groups_per_block=gpb, **launch)
     assert np.array_equal(s1[-1], states[-1])
     assert np.array_equal(one.indicator_numpy(0, t0), cs.indicator_numpy(0, t0))
     assert P.pbn_take_device_status() == 0
@@ -81,12 +86,12 @@ def test_balanced_launches_several_properties(P, sms):
     phase 2 start at its step offset)."""
     G = _groups(sms, 1, sms // 2)
     omega = 32 * G
-    net = S.random_pbn(41, 16, (1, 3), (2, 4), "fair", "uniform", 0.02)
+    net = S.random_pbn(41, 20, (1, 3), (2, 4), "fair", "uniform", 0.02)  # one-warp CTAs: 1 vs 2 rounds
     props = [S.StateOfInterest([0, 1], [1, 1]), S.StateOfInterest([5], [0])]
     N = P.pbn_load(net)
     cs = P.ChainSet(N, omega, bits_cap=100, n_props=2)
     P.pbn_init_chains(cs, 9, 0)
-    P.pbn_run_chains(cs, 100, 9, 0, props=props)
+    P.pbn_run_chains(cs, 100, 9, 0, props=props, threads_per_block=32)
     init = oracle.init_states(net, 9, omega)
     for m, soi in enumerate(props):
         ref, ind = oracle.simulate(net, 0, 9, init, 0, 100, soi)
