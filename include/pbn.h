@@ -183,6 +183,20 @@ int pbn_init_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *chai
 int pbn_run_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *chains, int64_t steps,
                    void *stream);
 
+/* The balanced split of one FUSED call into two launches (host arithmetic
+ * only, no device work; pbn_run_chains applies it with R = the device's SM
+ * count and its own launch shape).  Inputs: G chain groups, R SMs, CTAs of at
+ * most gpb groups with T threads per item and `threads` threads, an n-node
+ * network, k steps.  On *split = 1, launch[20] holds for launch 1 then
+ * launch 2, for segment 0 then 1, {CTAs, first group, groups, steps, step
+ * offset}; a segment's CTAs split its groups evenly (CTA b of nb takes groups
+ * first + b*groups/nb up to first + (b+1)*groups/nb - 1) and advance them
+ * `steps` transitions from transition length + offset.  *split = 0: one
+ * launch (launch untouched).  Errors: PBN_ERR_INVALID (NULL pointer, a size
+ * below 1, T not 1, 2 or 4, k < 0). */
+int pbn_balance_phases(int32_t G, int32_t R, int32_t gpb, int32_t T, int32_t threads, int32_t n, int64_t k,
+                       int32_t launch[20], int32_t *split);
+
 /* Simulation launches record a failed bounded device-side wait (a TMA tile
  * that did not arrive within 1 s) in a per-device status word instead of
  * waiting forever; the drivers check it after every query.  This call

@@ -176,6 +176,7 @@ def lib():
             L.pbn_net_get_info.argtypes = [c_vp, P(NetInfo)]
             L.pbn_init_chains.argtypes = [c_vp, P(RunCfg), P(Chains), c_vp]
             L.pbn_run_chains.argtypes = [c_vp, P(RunCfg), P(Chains), c_i64, c_vp]
+            L.pbn_balance_phases.argtypes = [c_i32, c_i32, c_i32, c_i32, c_i32, c_i32, c_i64, P(c_i32), P(c_i32)]
             L.pbn_gelman_rubin.argtypes = [P(Chains), c_i64, c_i64, c_vp, c_vp]
             L.pbn_two_state.argtypes = [P(Chains), c_i64, c_i64, c_dbl, c_dbl, c_dbl, c_vp, c_vp]
             L.pbn_skart.argtypes = [P(Chains), c_i64, c_i64, c_i64, c_i64, c_dbl, c_dbl, c_vp, c_vp]
@@ -369,6 +370,20 @@ def _cfg(seed, mode, soi_arg, groups_per_block=0, threads_per_block=0, threads_p
     return RunCfg(int(seed), int(mode), soi_arg.struct, int(groups_per_block), int(threads_per_block),
                   int(threads_per_item), int(blocks_per_round), STAGING[staging], SCHEDULE[schedule],
                   props_arg.count if props_arg else 0, props_arg.ptr if props_arg else None)
+
+
+def pbn_balance_phases(G: int, R: int, gpb: int, T: int, threads: int, n: int, k: int):
+    """The balanced split of one fused call (host arithmetic only): None for
+    one launch, else two launches, each a list of two segments
+    (CTAs, first group, groups, steps, step offset)."""
+    out = (c_i32 * 20)()
+    split = c_i32()
+    _check(lib().pbn_balance_phases(int(G), int(R), int(gpb), int(T), int(threads), int(n), int(k), out,
+                                    ctypes.byref(split)))
+    if not split.value:
+        return None
+    v = list(out)
+    return [[tuple(v[10 * l + 5 * q:10 * l + 5 * q + 5]) for q in range(2)] for l in range(2)]
 
 
 def pbn_take_device_status() -> int:

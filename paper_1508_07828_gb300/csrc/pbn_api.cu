@@ -604,6 +604,37 @@ int take_status(int *out) {
 }
 }  // namespace
 
+extern "C" int pbn_balance_phases(int32_t G, int32_t R, int32_t gpb, int32_t T, int32_t threads, int32_t n,
+                                  int64_t k, int32_t launch[20], int32_t *split) {
+  if (!launch || !split) return fail(PBN_ERR_INVALID, "NULL argument");
+  if (G < 1 || R < 1 || gpb < 1 || threads < 1 || n < 1 || k < 0)
+    return fail(PBN_ERR_INVALID, "sizes must be positive (G %d, R %d, gpb %d, threads %d, n %d, k %lld)", G, R, gpb,
+                threads, n, (long long)k);
+  if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
+  LaunchPlan plan{};
+  plan.gpb = gpb;
+  plan.threads = threads;
+  plan.T = T;
+  plan.BPR = 1;
+  pbn::SimArgs a1, a2;
+  memset(&a1, 0, sizeof a1);
+  memset(&a2, 0, sizeof a2);
+  *split = 0;
+  if (!balance_phases(G, R, plan, n, k, &a1, &a2)) return PBN_OK;
+  const pbn::SimArgs *ph[2] = {&a1, &a2};
+  for (int l = 0; l < 2; l++)
+    for (int q = 0; q < 2; q++) {
+      int32_t *o = launch + 10 * l + 5 * q;
+      o[0] = ph[l]->seg_blocks[q];
+      o[1] = ph[l]->seg_g0[q];
+      o[2] = ph[l]->seg_ng[q];
+      o[3] = ph[l]->seg_steps[q];
+      o[4] = ph[l]->seg_soff[q];
+    }
+  *split = 1;
+  return PBN_OK;
+}
+
 extern "C" int pbn_take_device_status(int *status) {
   if (!status) return fail(PBN_ERR_INVALID, "NULL argument");
   return take_status(status);
