@@ -67,3 +67,28 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     ns = type("A", (), dict(gpus=2, steps=1, warmup=0))()
     bench.run_reference(ns)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
+    """Rank 0 of the reference arm prints one JSON line with the contract's
+    keys, the oracle as its CPU baseline and the GPU arm's workload config."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    for k, v in (("WORLD_SIZE", "1"), ("RANK", "0"), ("LOCAL_RANK", "0")):
+        monkeypatch.setenv(k, v)
+    ns = type("A", (), dict(gpus=1, steps=1, warmup=3))()
+    bench.run_reference(ns)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["value"] > 0
+    assert d["steps"] == 1 and d["warmup"] == 3 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    net, _, cfg = bench.workload()
+    assert d["config"] == bench.config_dict(cfg, net)
