@@ -192,8 +192,10 @@ int pbn_run_chains(const pbn_net *net, const pbn_run_cfg *cfg, pbn_chains *chain
  * offset}; a segment's CTAs split its groups evenly (CTA b of nb takes groups
  * first + b*groups/nb up to first + (b+1)*groups/nb - 1) and advance them
  * `steps` transitions from transition length + offset.  *split = 0: one
- * launch (launch untouched).  Errors: PBN_ERR_INVALID (NULL pointer, a size
- * below 1, T not 1, 2 or 4, k < 0). */
+ * launch (launch untouched).  pbn_run_chains splits a call into launches of
+ * at most 2^30 steps first, so k is at most 2^30 here.  Errors:
+ * PBN_ERR_INVALID (NULL pointer, a size below 1, T not 1, 2 or 4, k outside
+ * 0 .. 2^30). */
 int pbn_balance_phases(int32_t G, int32_t R, int32_t gpb, int32_t T, int32_t threads, int32_t n, int64_t k,
                        int32_t launch[20], int32_t *split);
 

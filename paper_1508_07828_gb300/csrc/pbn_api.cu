@@ -607,9 +607,9 @@ int take_status(int *out) {
 extern "C" int pbn_balance_phases(int32_t G, int32_t R, int32_t gpb, int32_t T, int32_t threads, int32_t n,
                                   int64_t k, int32_t launch[20], int32_t *split) {
   if (!launch || !split) return fail(PBN_ERR_INVALID, "NULL argument");
-  if (G < 1 || R < 1 || gpb < 1 || threads < 1 || n < 1 || k < 0)
-    return fail(PBN_ERR_INVALID, "sizes must be positive (G %d, R %d, gpb %d, threads %d, n %d, k %lld)", G, R, gpb,
-                threads, n, (long long)k);
+  if (G < 1 || R < 1 || gpb < 1 || threads < 1 || n < 1 || k < 0 || k > (int64_t)1 << 30)
+    return fail(PBN_ERR_INVALID, "sizes must be positive, k at most 2^30 (G %d, R %d, gpb %d, threads %d, n %d, "
+                "k %lld)", G, R, gpb, threads, n, (long long)k);
   if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
   LaunchPlan plan{};
   plan.gpb = gpb;

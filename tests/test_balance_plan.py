@@ -81,7 +81,7 @@ def test_every_split_covers_every_group_in_order(P):
 
 @pytest.mark.parametrize("args", [(0, 152, 4, 1, 1024, 2000, 256), (512, 0, 4, 1, 1024, 2000, 256),
                                   (512, 152, 4, 3, 1024, 2000, 256), (512, 152, 4, 1, 1024, 2000, -1),
-                                  (512, 152, 4, 1, 0, 2000, 256)])
+                                  (512, 152, 4, 1, 0, 2000, 256), (512, 152, 4, 1, 1024, 2000, (1 << 30) + 1)])
 def test_invalid_arguments(P, args):
     with pytest.raises(P.PbnError) as e:
         P.pbn_balance_phases(*args)
