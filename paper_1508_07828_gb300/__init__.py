@@ -225,6 +225,28 @@ def _as_struct(cls, obj):
 
 # ------------------------------------------------------------------ network
 
+def _network_counts(n: int, a: dict, n_parents: int) -> int:
+    """The function count F to pass to pbn_load with the host arrays `a`
+    (numpy arrays or host tensors): the entries of select_prob.  pbn_load
+    reads every array up to the length that n and F imply, so arrays of any
+    other length are refused here."""
+    F = len(a["select_prob"])
+    sizes = [("fn_offset", n + 1), ("truth_table", F), ("par_offset", F + 1)]
+    if "tt_offset" in a:
+        sizes.append(("tt_offset", F + 1))
+    for name, want in sizes:
+        if len(a[name]) != want:
+            raise PbnError(PBN_ERR_INVALID, f"{name} has {len(a[name])} entries, {want} expected "
+                                            f"(n = {n}, {F} functions)")
+    ends = [("parents", "par_offset", n_parents)]
+    if "tt_offset" in a:
+        ends.append(("tt_words", "tt_offset", len(a["tt_words"])))
+    for name, off, have in ends:
+        if int(a[off][-1]) > have:
+            raise PbnError(PBN_ERR_INVALID, f"{name} has {have} entries, {off}[-1] = {int(a[off][-1])}")
+    return F
+
+
 class Network:
     """A PBN staged on the device (owns the pbn_net handle)."""
 
@@ -240,15 +262,16 @@ class Network:
             self._arrays["tt_offset"] = np.ascontiguousarray(net.tt_offset, dtype=np.int32)
             self._arrays["tt_words"] = np.ascontiguousarray(net.tt_words, dtype=np.uint32)
         a = self._arrays
-        desc = NetworkDesc(int(net.n), int(a["fn_offset"][-1]), a["fn_offset"].ctypes.data, a["par_offset"].ctypes.data,
+        n, F = int(net.n), _network_counts(int(net.n), a, len(net.parents))
+        desc = NetworkDesc(n, F, a["fn_offset"].ctypes.data, a["par_offset"].ctypes.data,
                            a["parents"].ctypes.data, a["truth_table"].ctypes.data, a["select_prob"].ctypes.data,
                            float(net.p), a["tt_offset"].ctypes.data if wide else None,
                            a["tt_words"].ctypes.data if wide else None)
         h = c_vp()
         _check(lib().pbn_load(ctypes.byref(desc), ctypes.byref(h)))
         self.handle = h
-        self.n = int(net.n)
-        self.n_functions = int(a["fn_offset"][-1])
+        self.n = n
+        self.n_functions = F
 
     def info(self) -> dict:
         o = NetInfo()
@@ -279,7 +302,8 @@ def pbn_load_pinned(host_arrays: dict, n: int, p: float) -> Network:
     self = Network.__new__(Network)
     self._arrays = host_arrays
     a = host_arrays
-    desc = NetworkDesc(int(n), int(a["fn_offset"][-1]), a["fn_offset"].data_ptr(), a["par_offset"].data_ptr(),
+    F = _network_counts(int(n), a, len(a["parents"]))
+    desc = NetworkDesc(int(n), F, a["fn_offset"].data_ptr(), a["par_offset"].data_ptr(),
                        a["parents"].data_ptr(), a["truth_table"].data_ptr(), a["select_prob"].data_ptr(), float(p),
                        a["tt_offset"].data_ptr() if "tt_offset" in a else None,
                        a["tt_words"].data_ptr() if "tt_words" in a else None)
@@ -287,7 +311,7 @@ def pbn_load_pinned(host_arrays: dict, n: int, p: float) -> Network:
     _check(lib().pbn_load(ctypes.byref(desc), ctypes.byref(h)))
     self.handle = h
     self.n = int(n)
-    self.n_functions = int(a["fn_offset"][-1])
+    self.n_functions = F
     return self
 
 

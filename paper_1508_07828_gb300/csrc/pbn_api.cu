@@ -668,9 +668,31 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
     return fail(PBN_ERR_INVALID, "NULL network array");
   if (!(d->p >= 0.0 && d->p < 1.0)) return fail(PBN_ERR_INVALID, "perturbation probability %g", d->p);
   const int F = d->n_functions;
-  if (d->fn_offset[0] != 0 || d->fn_offset[n] != F) return fail(PBN_ERR_INVALID, "fn_offset does not span F");
+  if (F < n) return fail(PBN_ERR_INVALID, "n_functions = %d for %d nodes", F, n);
   if (F > 65535) return fail(PBN_ERR_UNSUPPORTED, "F = %d exceeds 65535", F);
+  // offsets first, so that every read below stays inside the arrays' stated
+  // lengths: fn_offset [n+1], par_offset and tt_offset [F+1], the rest [F]
+  // or par_offset[F] / tt_offset[F]
+  if (d->fn_offset[0] != 0 || d->fn_offset[n] != F) return fail(PBN_ERR_INVALID, "fn_offset does not span F");
+  for (int i = 0; i < n; i++) {
+    const int l = d->fn_offset[i + 1] - d->fn_offset[i];
+    if (l < 1) return fail(PBN_ERR_INVALID, "node %d has no predictor function", i);
+    if (l > PBN_MAX_FUNCTIONS_PER_NODE)
+      return fail(PBN_ERR_UNSUPPORTED, "node %d has %d functions (max %d)", i, l, PBN_MAX_FUNCTIONS_PER_NODE);
+  }
   if (d->par_offset[0] != 0) return fail(PBN_ERR_INVALID, "par_offset[0] != 0");
+  for (int f = 0; f < F; f++) {
+    const int k = d->par_offset[f + 1] - d->par_offset[f];
+    if (k < 0) return fail(PBN_ERR_INVALID, "par_offset decreasing at %d", f);
+    if (k > PBN_MAX_PARENTS) return fail(PBN_ERR_UNSUPPORTED, "function %d has %d parents", f, k);
+  }
+  if (d->par_offset[F] > 0 && !d->parents) return fail(PBN_ERR_INVALID, "parents is NULL");
+  if (d->tt_offset) {
+    if (!d->tt_words) return fail(PBN_ERR_INVALID, "tt_words is NULL");
+    if (d->tt_offset[0] < 0) return fail(PBN_ERR_INVALID, "tt_offset[0] < 0");
+    for (int f = 0; f < F; f++)
+      if (d->tt_offset[f + 1] < d->tt_offset[f]) return fail(PBN_ERR_INVALID, "tt_offset decreasing at %d", f);
+  }
   const uint32_t P32 = quantise_p(d->p);
   const uint64_t span = 4294967296ull - P32;
   std::vector<uint4> fn(F);

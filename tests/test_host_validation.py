@@ -32,7 +32,7 @@ def _net(**over):
 def _status(P, net):
     with pytest.raises(P.PbnError) as e:
         P.pbn_load(net)
-    assert P.lib().pbn_last_error().decode()  # a message says why
+    assert str(e.value).split(":", 1)[1].strip()  # a message says why
     return e.value.status
 
 
@@ -49,6 +49,67 @@ def test_structure_is_checked(P):
     fo = _net().fn_offset.copy()
     fo[1] = fo[0]  # node 0 without a predictor function
     assert _status(P, _net(fn_offset=fo)) == P.PBN_ERR_INVALID
+
+
+def test_offsets_are_checked_before_reading_through_them(P):
+    """Offsets that stay inside [0, F] at both ends but would lead a later
+    node or function past the arrays' ends are refused first (3 nodes,
+    4 functions, 6 parents)."""
+    assert _status(P, _net(fn_offset=np.array([0, 3, 5, 4], np.int32))) == P.PBN_ERR_INVALID
+    assert _status(P, _net(fn_offset=np.array([0, 2, 1, 4], np.int32))) == P.PBN_ERR_INVALID
+    # function 0 claims 7 parents of the 6, function 1 then goes backwards
+    assert _status(P, _net(par_offset=np.array([0, 7, 3, 4, 6], np.int32))) == P.PBN_ERR_INVALID
+    assert _status(P, _net(par_offset=np.array([1, 2, 3, 4, 6], np.int32))) == P.PBN_ERR_INVALID
+    wide = _net()
+    wide.tt_offset = np.array([0, 2, 1, 3, 4], np.int32)
+    wide.tt_words = np.zeros(4, np.uint32)
+    assert _status(P, wide) == P.PBN_ERR_INVALID
+
+
+def test_array_lengths_are_checked_by_the_binding(P):
+    """The function count passed to pbn_load is the arrays' own, and arrays
+    shorter or longer than the counts imply are refused before the call."""
+    base = _net()
+    assert _status(P, _net(select_prob=base.select_prob[:3])) == P.PBN_ERR_INVALID
+    assert _status(P, _net(truth_table=base.truth_table[:3])) == P.PBN_ERR_INVALID
+    assert _status(P, _net(par_offset=base.par_offset[:4])) == P.PBN_ERR_INVALID
+    assert _status(P, _net(fn_offset=np.array([0, 1, 3, 4, 4], np.int32))) == P.PBN_ERR_INVALID
+    assert _status(P, _net(parents=base.parents[:5])) == P.PBN_ERR_INVALID
+    wide = _net()
+    wide.tt_offset = np.arange(5, dtype=np.int32)
+    wide.tt_words = np.zeros(3, np.uint32)
+    assert _status(P, wide) == P.PBN_ERR_INVALID
+
+
+def _networks_of_every_recipe():
+    yield S.three_node(1 / 16)
+    yield S.identity_node(0.01)
+    yield S.constant_node(0.01)
+    yield S.all_identity(12, 0.01)
+    yield S.tiny_config()[0]
+    yield S.mid_config()[0]
+    yield S.large_config()[0]
+    yield S.wide_config()[0]
+    for n in (80, 100, 200, 500, 1000, 2000):
+        for density in ("sparse", "in-between"):
+            yield S.sweep_config(n, density)[0]
+    for net, _, _ in S.batch_configs():
+        yield net
+    yield from S.serving_pool()
+
+
+def test_every_synthetic_recipe_passes_validation(P):
+    """Every network the tests and the bench stage passes pbn_load's checks:
+    without a GPU the call fails only at the device copy (PBN_ERR_CUDA), with
+    one it loads."""
+    count = 0
+    for net in _networks_of_every_recipe():
+        try:
+            P.pbn_load(net).close()
+        except P.PbnError as e:
+            assert e.status == P.PBN_ERR_CUDA, (getattr(net, "name", "?"), str(e))
+        count += 1
+    assert count > 270
 
 
 def test_probabilities_are_checked(P):
