@@ -320,8 +320,11 @@ class SoiArg:
         if soi is None:
             self.nodes = np.zeros(1, np.int32); self.values = np.zeros(1, np.uint8); self.size = 0
         else:
-            self.nodes = np.ascontiguousarray(soi.nodes, dtype=np.int32)
-            self.values = np.ascontiguousarray(soi.values, dtype=np.uint8)
+            self.nodes = np.ascontiguousarray(soi.nodes, dtype=np.int32).reshape(-1)
+            self.values = np.ascontiguousarray(soi.values, dtype=np.uint8).reshape(-1)
+            if len(self.values) != len(self.nodes):  # the C call reads `size` entries of each
+                raise PbnError(PBN_ERR_INVALID, f"state of interest: {len(self.nodes)} nodes, "
+                                                f"{len(self.values)} values")
             self.size = len(self.nodes)
         self.struct = Soi(self.size, self.nodes.ctypes.data, self.values.ctypes.data)
 

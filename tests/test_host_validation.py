@@ -81,6 +81,15 @@ def test_array_lengths_are_checked_by_the_binding(P):
     assert _status(P, wide) == P.PBN_ERR_INVALID
 
 
+def test_state_of_interest_lengths_are_checked_by_the_binding(P):
+    """pbn_soi carries one size for its two arrays: nodes and values of
+    different lengths are refused before any call."""
+    for nodes, values in (([0, 1], [1]), ([0], [1, 0])):
+        with pytest.raises(P.PbnError) as e:
+            P.SoiArg(types.SimpleNamespace(nodes=np.array(nodes), values=np.array(values)))
+        assert e.value.status == P.PBN_ERR_INVALID
+
+
 def _networks_of_every_recipe():
     yield S.three_node(1 / 16)
     yield S.identity_node(0.01)
