@@ -256,7 +256,10 @@ typedef struct pbn_skart_result {
  * positions from `start`; computes the von Neumann randomness test on the
  * spaced batch means (spacer `spacer`, size alpha_ran) and the skewness- and
  * autoregression-adjusted CI of the nonspaced batch means at level
- * 1 - alpha_ci.  out: device pointer, written asynchronously. */
+ * 1 - alpha_ci.  out: device pointer, written asynchronously.  Errors:
+ * PBN_ERR_INVALID (window outside the recorded positions, kappa or
+ * batches_per_chain below 1, spacer below 0, fewer than 2 batches),
+ * PBN_ERR_UNSUPPORTED (kappa above 2^30, batches_per_chain above 2^32). */
 int pbn_skart(const pbn_chains *chains, int64_t start, int64_t kappa, int64_t batches_per_chain,
               int64_t spacer, double alpha_ci, double alpha_ran, pbn_skart_result *out, void *stream);
 

@@ -909,6 +909,7 @@ int pbn_skart(const pbn_chains *ch, int64_t start, int64_t kappa, int64_t bpc, i
               double alpha_ran, pbn_skart_result *out, void *stream) {
   if (kappa < 1 || bpc < 1 || spacer < 0) return fail(PBN_ERR_INVALID, "kappa, batches, spacer");
   if (kappa > (1ll << 30)) return fail(PBN_ERR_UNSUPPORTED, "batch size above 2^30");
+  if (bpc > (1ll << 32)) return fail(PBN_ERR_UNSUPPORTED, "batches per chain above 2^32");  // kappa * bpc < 2^63
   int rc = check_window(ch, start, kappa * bpc);
   if (rc) return rc;
   if (ch->omega * bpc < 2) return fail(PBN_ERR_INVALID, "Skart needs at least 2 batches");

@@ -90,6 +90,33 @@ def test_state_of_interest_lengths_are_checked_by_the_binding(P):
         assert e.value.status == P.PBN_ERR_INVALID
 
 
+def test_statistics_windows_and_parameters_are_checked(P):
+    """The statistics entry points check the window against the recorded
+    positions and their parameters before any device work (here a chain set
+    whose device pointers are never dereferenced)."""
+    import ctypes
+    L = P.lib()
+    ch = P.Chains(64, 16, 16, 1000, 100, 900)  # omega 64; positions 100 .. 899 recorded, capacity 1000
+    out = ctypes.c_void_p(16)
+    cases = [
+        (L.pbn_gelman_rubin, (ctypes.byref(ch), 99, 100, out, None), P.PBN_ERR_INVALID),    # before bits_base
+        (L.pbn_gelman_rubin, (ctypes.byref(ch), 800, 101, out, None), P.PBN_ERR_INVALID),   # past the length
+        (L.pbn_gelman_rubin, (ctypes.byref(ch), 100, 1, out, None), P.PBN_ERR_INVALID),     # psi < 2
+        (L.pbn_two_state, (ctypes.byref(ch), 100, 0, 1e-10, 0.01, 0.95, out, None), P.PBN_ERR_INVALID),
+        (L.pbn_two_state, (ctypes.byref(ch), 100, 50, 1e-10, 0.01, 1.0, out, None), P.PBN_ERR_INVALID),
+        (L.pbn_skart, (ctypes.byref(ch), 100, 0, 1, 0, 0.05, 0.2, out, None), P.PBN_ERR_INVALID),
+        (L.pbn_skart, (ctypes.byref(ch), 100, 10, 81, 0, 0.05, 0.2, out, None), P.PBN_ERR_INVALID),
+        (L.pbn_skart, (ctypes.byref(ch), 100, (1 << 30) + 1, 1, 0, 0.05, 0.2, out, None), P.PBN_ERR_UNSUPPORTED),
+        (L.pbn_skart, (ctypes.byref(ch), 100, 1 << 30, (1 << 32) + 1, 0, 0.05, 0.2, out, None),
+         P.PBN_ERR_UNSUPPORTED),
+        (L.pbn_skart_static, (ctypes.byref(ch), 100, 10, 81, 0, 0.05, 0.2, out, None), P.PBN_ERR_INVALID),
+        (L.pbn_skart_static, (ctypes.byref(ch), 100, 1, 1 << 13, 0, 0.05, 0.2, out, None), P.PBN_ERR_UNSUPPORTED),
+    ]
+    for fn, args, want in cases:
+        assert fn(*args) == want, (fn.__name__, args[1:4])
+        assert L.pbn_last_error().decode()
+
+
 def _networks_of_every_recipe():
     yield S.three_node(1 / 16)
     yield S.identity_node(0.01)
