@@ -553,10 +553,6 @@ def pbn_estimate_skart_seq(network: Network, soi, seed: int, H_star: float, rela
 
 # ------------------------------------------------------------------ engine
 
-def _report(cls, obj):
-    return _as_struct(cls, obj)
-
-
 class Engine:
     """Batched / served queries (pbn_engine_* in include/pbn.h): queries of
     uneven size advance together, one persistent simulation launch and one

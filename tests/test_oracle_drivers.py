@@ -97,3 +97,19 @@ def test_constant_node_alpha_beta_not_swapped(orc):
                                  psi0=256, rhat=1.1, r=0.005, s=0.95, mode=0)
     assert out["alpha"] == 1.0
     assert abs(out["beta"] - 0.05) < 0.01
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_periodic_chain_is_not_converged(orc, mode):
+    """NOT node: under both perturbation readings the node flips at every
+    step, so the indicator alternates.  Every chain then has psi/2 ones in
+    each window: B = 0 and R-hat = sqrt(1 - 1/psi) exactly (Alg. GR), every
+    transition is 0->1 or 1->0 (alpha = beta = 1), and Alg. 3 cannot size a
+    sample: PBN_ERR_NOT_CONVERGED."""
+    omega, psi0 = 8, 64
+    out = orc.estimate_two_state(S.not_node(0.05), S.StateOfInterest([0], [1]), omega=omega, seed=3, psi0=psi0,
+                                 rhat=1.1, r=0.01, s=0.95, mode=mode)
+    assert out["status"] == 5
+    assert out["rhat"] == pytest.approx(np.sqrt(1 - 1 / psi0), rel=1e-15)
+    half = omega * (psi0 - 1) // 2
+    assert out["n4"] == [0, half, half, 0]
