@@ -14,11 +14,14 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
   philox4x32_10      cuRAND's host Philox4_32_10 generator (library outputs)
   simulate/init      exact one-step transition law of exact.py (chi-square),
                      exact stationary distributions, hand-built 3-node PBN
+  exact (n <= 16)    dense step = implicit step at n = 10..12; uniform law and
+                     its closed-form transient on all-identity networks; the
+                     product of five exact 3-node laws at n = 16
   gelman_rubin       closed form from integer sums; numpy; R-hat -> 1 on iid
   two_state_MN       closed forms on the identity / constant node
   norm_ppf, t_ppf    scipy.stats norm.ppf / t.ppf
   skewness           scipy.stats.skew
-  estimate_two_state exact answers on small networks (within r)
+  estimate_two_state exact answers on small networks (within r), up to n = 16
   estimate_two_state_seq
                      Alg. 1 on one chain: the stopping rule, an independent
                      replay of the final window, exact answers within r,

@@ -182,6 +182,16 @@ def mid_config(seed: int = BASE_SEED + 1) -> tuple:
     return net, soi, dict(omega=1024, rhat=1.05, r=0.005, s=0.95, eps=1e-10)
 
 
+def exact_config(n: int = 16, seed: int = BASE_SEED + 16) -> tuple:
+    """A network small enough for the exact solver's implicit step (n <= 16):
+    1-3 functions per node, 1-3 parents, biased truth tables, p = 0.05 (fast
+    mixing, so FP64 power iteration converges in a few hundred steps); 64
+    chains; state of interest nodes {0,1,2} = (1,0,1); r = 0.01."""
+    net = random_pbn(seed, n, (1, 3), (1, 3), "biased", "uniform", 0.05, f"exact-n{n}")
+    soi = StateOfInterest([0, 1, 2], [1, 0, 1])
+    return net, soi, dict(omega=64, psi0=256, rhat=1.05, r=0.01, s=0.95, eps=1e-10)
+
+
 def large_config(seed: int = BASE_SEED + 2, n: int = 2000) -> tuple:
     """n=2000; 1-4 functions; 2-5 parents drawn with scale-free weights;
     biased truth tables; p=0.001; 16384 chains; Skart at relative precision
