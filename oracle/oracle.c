@@ -786,30 +786,39 @@ double orc_skewness(const double *v, int64_t K) {
     return m3 / pow(m2, 1.5);
 }
 
-/* Regularised incomplete beta I_x(a,b) by the continued fraction of its
- * definition (evaluated with the modified Lentz method). */
-static double betacf(double a, double b, double x) {
-    const double tiny = 1e-300;
-    double qab = a + b, qap = a + 1.0, qam = a - 1.0;
-    double c = 1.0, d = 1.0 - qab * x / qap;
-    if (fabs(d) < tiny) d = tiny;
-    d = 1.0 / d;
-    double h = d;
-    for (int m = 1; m <= 100000; m++) {
-        int m2 = 2 * m;
-        double aa = m * (b - m) * x / ((qam + m2) * (a + m2));
-        d = 1.0 + aa * d; if (fabs(d) < tiny) d = tiny;
-        c = 1.0 + aa / c; if (fabs(c) < tiny) c = tiny;
-        d = 1.0 / d; h *= d * c;
-        aa = -(a + m) * (qab + m) * x / ((a + m2) * (qap + m2));
-        d = 1.0 + aa * d; if (fabs(d) < tiny) d = tiny;
-        c = 1.0 + aa / c; if (fabs(c) < tiny) c = tiny;
-        d = 1.0 / d;
-        double del = d * c;
-        h *= del;
-        if (fabs(del - 1.0) < 1e-16) break;
+/* The continued fraction of the regularised incomplete beta function
+ * (DLMF 8.17.22):
+ *   I_x(a,b) = x^a (1-x)^b / (a B(a,b)) * 1/(1 + d_1/(1 + d_2/(1 + ...))),
+ *   d_{2m}   =  m (b - m) x / ((a + 2m - 1)(a + 2m)),
+ *   d_{2m+1} = -(a + m)(a + b + m) x / ((a + 2m)(a + 2m + 1)).
+ * cf_term(j) is d_j. */
+static double cf_term(double a, double b, double x, long j) {
+    double m = (double)(j / 2);
+    if (j % 2 == 0) return m * (b - m) * x / ((a + 2.0 * m - 1.0) * (a + 2.0 * m));
+    return -(a + m) * (a + b + m) * x / ((a + 2.0 * m) * (a + 2.0 * m + 1.0));
+}
+
+/* Value of 1/(1 + d_1/(1 + d_2/(1 + ...))) as the limit of its convergents
+ * A_j / B_j, which obey the fundamental (Wallis) recurrences
+ * A_j = A_{j-1} + d_{j-1} A_{j-2}, B_j = B_{j-1} + d_{j-1} B_{j-2} from
+ * A_0 = 0, A_1 = 1, B_0 = 1, B_1 = 1.  Each step divides the last two pairs
+ * by the new B_j, so B_j stays 1 and A_j is the convergent itself. */
+static double cf_value(double a, double b, double x) {
+    double A_older = 0.0, A_old = 1.0, B_older = 1.0;
+    double value = 1.0;
+    for (long j = 2; j < 400000; j++) {
+        double d = cf_term(a, b, x, j - 1);
+        double A = A_old + d * A_older;
+        double B = 1.0 + d * B_older;          /* B_{j-1} is 1 after rescaling */
+        if (B == 0.0) B = 1e-300;
+        A_older = A_old / B;
+        B_older = 1.0 / B;
+        A_old = A / B;
+        double change = fabs(A_old - value);
+        value = A_old;
+        if (change <= 1e-16 * fabs(value)) break;
     }
-    return h;
+    return value;
 }
 
 /* log Gamma(a+b) - log Gamma(a) without cancellation for large a: the
@@ -826,16 +835,30 @@ static double lgamma_ratio(double a, double b) {
     return (a - 0.5) * log1p(b / a) + b * log(a + b) - b + (stirling_tail(a + b) - stirling_tail(a));
 }
 
-/* Regularised incomplete beta I_x(a,b) with y = 1 - x supplied exactly. */
+/* ln B(p,q) = ln Gamma(s) - [ln Gamma(g+s) - ln Gamma(g)], g the larger and s
+ * the smaller argument, so that the difference of two large ln Gamma values is
+ * formed by lgamma_ratio without cancellation. */
+static double log_beta(double p, double q) {
+    double g = p > q ? p : q, sm = p > q ? q : p;
+    return lgamma(sm) - lgamma_ratio(g, sm);
+}
+
+/* Regularised incomplete beta I_x(a,b), y = 1 - x given exactly.  The
+ * fraction converges fast for x < (a+1)/(a+b+2) (DLMF 8.17(v)); otherwise the
+ * reflection I_x(a,b) = 1 - I_y(b,a) (DLMF 8.17.4) moves x below that point. */
 static double inc_beta(double a, double b, double x, double y) {
     if (x <= 0.0) return 0.0;
     if (y <= 0.0) return 1.0;
-    /* ln of x^a y^b / B(a,b) with ln B(a,b) = ln Gamma(b) - [ln Gamma(a+b) - ln Gamma(a)] */
-    double lnx = x > 0.5 ? log1p(-y) : log(x);
-    double lbt = lgamma_ratio(a, b) - lgamma(b) + a * lnx + b * log(y);
-    double bt = exp(lbt);
-    if (x < (a + 1.0) / (a + b + 2.0)) return bt * betacf(a, b, x) / a;
-    return 1.0 - bt * betacf(b, a, y) / b;
+    int reflect = !(x < (a + 1.0) / (a + b + 2.0));
+    double p = reflect ? b : a, q = reflect ? a : b;
+    double u = reflect ? y : x, w = reflect ? x : y;      /* w = 1 - u */
+    /* ln(u^p w^q / (p B(p,q))); the log of whichever of u, w is near 1 is
+     * taken as log1p of minus the other, which is exact to rounding */
+    double ln_u = u > 0.5 ? log1p(-w) : log(u);
+    double ln_w = w > 0.5 ? log1p(-u) : log(w);
+    double ln_front = p * ln_u + q * ln_w - log(p) - log_beta(p, q);
+    double I = exp(ln_front) * cf_value(p, q, u);
+    return reflect ? 1.0 - I : I;
 }
 
 /* Student t CDF with dof degrees of freedom:

@@ -125,41 +125,61 @@ __device__ inline double ln_gamma_ratio(double a, double b) {
   return (a - 0.5) * log1p(b / a) + b * log(a + b) - b + (tail(a + b) - tail(a));
 }
 
-// Continued fraction of the regularised incomplete beta function
-// (even/odd coefficients d_2m, d_2m+1), modified Lentz evaluation.
-__device__ inline double beta_cfrac(double a, double b, double x) {
-  const double tiny = 1e-300;
-  double f = 1.0, C = 1.0, D = 1.0 - (a + b) * x / (a + 1.0);
-  D = fabs(D) < tiny ? 1.0 / tiny : 1.0 / D;
-  f = D;
-  for (int m = 1; m < 20000; m++) {
-    const double dm = m;
-    const double e = dm * (b - dm) * x / ((a + 2.0 * dm - 1.0) * (a + 2.0 * dm));
-    D = 1.0 + e * D; D = fabs(D) < tiny ? 1.0 / tiny : 1.0 / D;
-    C = 1.0 + e / C; if (fabs(C) < tiny) C = tiny;
-    f *= C * D;
-    const double o = -(a + dm) * (a + b + dm) * x / ((a + 2.0 * dm) * (a + 2.0 * dm + 1.0));
-    D = 1.0 + o * D; D = fabs(D) < tiny ? 1.0 / tiny : 1.0 / D;
-    C = 1.0 + o / C; if (fabs(C) < tiny) C = tiny;
-    const double r = C * D;
-    f *= r;
-    if (fabs(r - 1.0) < 2e-16) break;
+// Regularised incomplete beta function I_x(a, b) from its continued fraction
+// (DLMF 8.17.22): I_x(a,b) = x^a (1-x)^b / (a B(a,b)) K, where
+// K = 1/(1 + d_1/(1 + d_2/(1 + ...))) with
+//   d_{2m}   =  m (b - m) x / ((a + 2m - 1)(a + 2m)),
+//   d_{2m+1} = -(a + m)(a + b + m) x / ((a + 2m)(a + 2m + 1)).
+// K is the limit of the convergents P_j / Q_j, P_j = P_{j-1} + d_{j-1} P_{j-2}
+// and Q_j likewise (P_0 = 0, P_1 = 1, Q_0 = Q_1 = 1).  Each pass of the loop
+// below advances two convergents (one even and one odd coefficient) and then
+// divides the kept pairs by the newest Q, so the newest P is the convergent.
+__device__ inline double ibeta_fraction(double a, double b, double x) {
+  double p2 = 0.0, p1 = 1.0;  // P_{j-2}, P_{j-1}; Q_{j-1} = 1 after scaling
+  double q2 = 1.0;            // Q_{j-2}
+  double last = 1.0;
+  for (int m = 1; m < 100000; ++m) {
+    const double fm = (double)m;
+    const double c_odd = -(a + fm - 1.0) * (a + b + fm - 1.0) * x / ((a + 2.0 * fm - 2.0) * (a + 2.0 * fm - 1.0));
+    const double c_even = fm * (b - fm) * x / ((a + 2.0 * fm - 1.0) * (a + 2.0 * fm));
+    // d_{2m-1} (for m = 1: d_1 = -(a+b) x / (a+1), the odd formula at index 0)
+    double pn = p1 + c_odd * p2, qn = 1.0 + c_odd * q2;
+    if (qn == 0.0) qn = 1e-300;
+    p2 = p1 / qn; q2 = 1.0 / qn; p1 = pn / qn;
+    // d_{2m}
+    pn = p1 + c_even * p2; qn = 1.0 + c_even * q2;
+    if (qn == 0.0) qn = 1e-300;
+    p2 = p1 / qn; q2 = 1.0 / qn; p1 = pn / qn;
+    if (fabs(p1 - last) <= 1e-16 * fabs(p1)) break;
+    last = p1;
   }
-  return f;
+  return p1;
 }
 
-// P(|T| > t) / 2 for Student t with nu degrees of freedom (t >= 0):
+// I_x(a, b) with y = 1 - x given exactly.  The fraction is used where it
+// converges fast, x < (a+1)/(a+b+2); elsewhere I_x(a,b) = 1 - I_y(b,a).
+__device__ inline double reg_incomplete_beta(double a, double b, double x, double y) {
+  if (x <= 0.0) return 0.0;
+  if (y <= 0.0) return 1.0;
+  const bool flip = !(x < (a + 1.0) / (a + b + 2.0));
+  const double ea = flip ? b : a, eb = flip ? a : b;
+  const double ex = flip ? y : x, ey = flip ? x : y;
+  // logs of ex and ey; the one near 1 from log1p of the other, exact to rounding
+  const double lx = ex > 0.5 ? log1p(-ey) : log(ex);
+  const double ly = ey > 0.5 ? log1p(-ex) : log(ey);
+  // ln B(ea, eb) through the larger argument, so no two large ln Gamma cancel
+  const double big = fmax(ea, eb), small = fmin(ea, eb);
+  const double lnB = lgamma(small) - ln_gamma_ratio(big, small);
+  const double I = exp(ea * lx + eb * ly - log(ea) - lnB) * ibeta_fraction(ea, eb, ex);
+  return flip ? 1.0 - I : I;
+}
+
+// P(T > t) for Student t with nu degrees of freedom (t >= 0):
 // I_x(nu/2, 1/2) / 2 with x = nu/(nu + t^2), 1 - x = t^2/(nu + t^2).
 __device__ inline double student_upper_tail(double t, double nu) {
-  const double a = 0.5 * nu, b = 0.5;
   const double x = nu / (nu + t * t), y = (t * t) / (nu + t * t);
   if (y <= 0.0) return 0.5;
-  const double lnx = x > 0.5 ? log1p(-y) : log(x);
-  const double front = exp(ln_gamma_ratio(a, b) - lgamma(b) + a * lnx + b * log(y));
-  double I;
-  if (x < (a + 1.0) / (a + b + 2.0)) I = front * beta_cfrac(a, b, x) / a;
-  else I = 1.0 - front * beta_cfrac(b, a, y) / b;
-  return 0.5 * I;
+  return 0.5 * reg_incomplete_beta(0.5 * nu, 0.5, x, y);
 }
 
 // Student t quantile: Newton on the upper tail from the normal quantile.

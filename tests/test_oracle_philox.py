@@ -3,7 +3,7 @@ implementation: cuRAND's host-side PHILOX4_32_10 generator, run as a library
 on the CPU.  That generator emits block b of its stream as Philox of the
 counter (b >> 16 as a 64-bit value in words 0-1, b & 0xFFFF in word 2, 0) under
 the key (seed lo32, seed hi32), which exercises the key and counter words 0-2.
-Word 3 is covered on the GPU against cuRAND's device API (test_gpu_rng.py).
+Word 3 is pinned on the GPU against cuRAND's device API (tests/test_gpu_rng.py).
 """
 import ctypes
 import os
