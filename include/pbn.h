@@ -275,12 +275,16 @@ int pbn_skart(const pbn_chains *chains, int64_t start, int64_t kappa, int64_t ba
  * library's device image, which every GPU that loads the library holds until
  * the process exits.  The caller still passes the chains and the result slot.
  * The first call on a device looks up the array's device address (make that
- * first call before any stream capture).  All calls share the one array:
+ * first call before any stream capture); CUDA loads the library's device
+ * code lazily, so that first call also loads it and reserves the 1 MiB array
+ * on the device, and can fail with PBN_ERR_CUDA when device memory is short.
+ * Later calls on that device allocate nothing.  All calls share the one array:
  * calls whose work overlaps on the GPU (different streams, or other host
  * threads) race and must be serialised by the caller.  Each call overwrites
  * every batch sum it reads, so nothing needs clearing between calls.
  * Errors: PBN_ERR_UNSUPPORTED when omega * batches_per_chain exceeds
- * PBN_SKART_STATIC_MAX_BATCHES, otherwise as pbn_skart. */
+ * PBN_SKART_STATIC_MAX_BATCHES or kappa exceeds 2^30, PBN_ERR_INVALID as
+ * pbn_skart, PBN_ERR_CUDA. */
 int pbn_skart_static(const pbn_chains *chains, int64_t start, int64_t kappa, int64_t batches_per_chain,
                      int64_t spacer, double alpha_ci, double alpha_ran, pbn_skart_result *out, void *stream);
 

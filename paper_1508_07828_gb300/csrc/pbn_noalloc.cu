@@ -42,21 +42,31 @@ extern "C" int pbn_skart_static(const pbn_chains *ch, int64_t start, int64_t kap
     snprintf(g_msg, sizeof g_msg, "pbn_skart_static: NULL chains, bitstream or result");
     return reject(PBN_ERR_INVALID);
   }
-  if (kappa < 1 || bpc < 1 || spacer < 0 || kappa > (1ll << 30)) {
+  if (kappa < 1 || bpc < 1 || spacer < 0) {
     snprintf(g_msg, sizeof g_msg, "pbn_skart_static: kappa %lld, batches %lld, spacer %lld out of range",
              (long long)kappa, (long long)bpc, (long long)spacer);
     return reject(PBN_ERR_INVALID);
   }
-  if (ch->omega < 1 || ch->omega * bpc < 2) {
-    snprintf(g_msg, sizeof g_msg, "pbn_skart_static: needs at least 2 batches");
+  if (kappa > (1ll << 30)) {
+    snprintf(g_msg, sizeof g_msg, "pbn_skart_static: kappa %lld above 2^30", (long long)kappa);
+    return reject(PBN_ERR_UNSUPPORTED);
+  }
+  if (ch->omega < 1) {
+    snprintf(g_msg, sizeof g_msg, "pbn_skart_static: omega %lld below 1", (long long)ch->omega);
     return reject(PBN_ERR_INVALID);
   }
+  // capacity before any product of the two sizes, so that the product below
+  // cannot overflow
   if (ch->omega > kStaticBatches / bpc) {
     snprintf(g_msg, sizeof g_msg,
              "pbn_skart_static: %lld chains x %lld batches exceed the fixed capacity of %lld batch sums; "
              "use pbn_skart",
              (long long)ch->omega, (long long)bpc, (long long)kStaticBatches);
     return reject(PBN_ERR_UNSUPPORTED);
+  }
+  if (ch->omega * bpc < 2) {
+    snprintf(g_msg, sizeof g_msg, "pbn_skart_static: needs at least 2 batches");
+    return reject(PBN_ERR_INVALID);
   }
   const int64_t len = kappa * bpc;
   if (start < ch->bits_base || start + len - ch->bits_base > ch->bits_cap || start + len > ch->length) {

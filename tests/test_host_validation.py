@@ -111,6 +111,11 @@ def test_statistics_windows_and_parameters_are_checked(P):
          P.PBN_ERR_UNSUPPORTED),
         (L.pbn_skart_static, (ctypes.byref(ch), 100, 10, 81, 0, 0.05, 0.2, out, None), P.PBN_ERR_INVALID),
         (L.pbn_skart_static, (ctypes.byref(ch), 100, 1, 1 << 13, 0, 0.05, 0.2, out, None), P.PBN_ERR_UNSUPPORTED),
+        # kappa above 2^30 is beyond the build's limits, as in pbn_skart
+        (L.pbn_skart_static, (ctypes.byref(ch), 100, (1 << 30) + 1, 1, 0, 0.05, 0.2, out, None),
+         P.PBN_ERR_UNSUPPORTED),
+        # a batch count whose product with omega overflows 64 bits is refused by capacity
+        (L.pbn_skart_static, (ctypes.byref(ch), 100, 1, 1 << 62, 0, 0.05, 0.2, out, None), P.PBN_ERR_UNSUPPORTED),
     ]
     for fn, args, want in cases:
         assert fn(*args) == want, (fn.__name__, args[1:4])

@@ -37,9 +37,13 @@ def _same(a, b):
 
 def test_static_matches_allocating_entry_point_twice_in_a_row(P):
     N, cs = _chains(P)
-    # two consecutive calls with different batch layouts: the second call must
-    # not see anything the first one left in the shared array
-    for start, kappa, bpc, spacer in [(100, 8, 80, 1), (50, 3, 250, 0)]:
+    # consecutive calls with different batch layouts: no call may see what an
+    # earlier one left in the shared array.  Small after large and the same
+    # batch count with another kappa leave stale sums exactly where a read
+    # past the call's own batches would find them.
+    layouts = [(100, 8, 80, 1), (50, 3, 250, 0), (100, 8, 80, 1), (60, 6, 100, 2), (60, 7, 100, 2),
+               (100, 8, 80, 1)]
+    for start, kappa, bpc, spacer in layouts:
         got = P.pbn_skart_static(cs, start, kappa, bpc, spacer, 0.05, 0.20)
         ref = P.pbn_skart(cs, start, kappa, bpc, spacer, 0.05, 0.20)
         _same(got, ref)
