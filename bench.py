@@ -1,25 +1,35 @@
 #!/usr/bin/env python
-"""Throughput of the parallel steady-state method on one GB300.
+"""Throughput of the parallel steady-state method on one GB300: batched
+against plain.
 
-One step = one whole query of the hot path on the mid-size workload
-(n = 100 nodes, 2 functions per node, 2-5 parents, p = 0.001, 1024 chains,
-5-node state of interest): chain initialisation, the Gelman & Rubin burn-in
-(Alg. GR, R-hat < 1.05) and the parallel two-state Markov chain approach
-(Alg. 3, r = 0.005, s = 0.95, eps = 1e-10) up to the estimate.  Each step uses
-its own seed.  The metric is chain-node updates per second (omega x chain
-length x n over the query time), with the p50/p99 query latency beside it.
+One step = one pass of the batched workload: 64 independent PBNs (n
+log-uniform in [50, 3000], 256-4096 chains log-uniform, 2 functions per node,
+2-5 parents, p in {0.001, 0.01}), each a whole query of the hot path: chain
+initialisation, the Gelman & Rubin burn-in (Alg. GR, R-hat < 1.05) and the
+parallel two-state Markov chain approach (Alg. 3, r = 0.005, s = 0.95,
+eps = 1e-10) up to the estimate.  The batched form runs all 64 queries in the
+engine (one persistent simulation launch per epoch under a captured CUDA
+graph, autotuned); the plain form runs the same 64 queries (same seeds, the
+same chain-node updates) one network at a time through
+pbn_estimate_two_state.  The metric is chain-node updates per second (the sum
+of omega x chain length x n over the step's time) with the p50/p99 query
+latency beside it; `value` is the batched form's, `plain` the loop's.
 
-Timing: CUDA events on the query's stream around every step, W warm-up steps
-first; L2 is flushed (a 256 MB write) between timed steps, outside the events.
-`e2e` repeats the measurement through the C ABI with the network's CSR arrays
-in pinned host memory copied to the device inside the timed region.
+Timing: CUDA events on the current stream around every step (the engine and
+the drivers synchronise their streams, so the events bracket the whole job),
+W warm-up steps first (they also settle the engine's autotuner); L2 is
+flushed (a 256 MB write) between timed steps, outside the events.  `e2e`
+repeats the batched step through the C ABI with the 64 networks' CSR arrays
+in pinned host memory, staged on the device inside the timed region, and the
+results read back on the host.
 
 --impl reference times the CPU oracle (single-threaded C) on bounded samples
-of the same workload (the simulation of all 1024 chains for a fixed number of
-transitions per step).
+of the same workload: all chains of all 64 networks for a fixed number of
+transitions per step.  --mid measures the single mid-size query (n = 100,
+1024 chains) instead; the default line carries it as `mid_query`.
 
 Multi-GPU: the queries are independent, so N ranks run N replicas of the
-query stream (weak scaling); ranks only meet at the barriers and the final
+workload (weak scaling); ranks only meet at the barriers and the final
 max-over-ranks of the timed region.
 """
 import argparse
@@ -39,6 +49,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "chain-node updates/s"
 WORKLOAD = "mid-n100-omega1024-two-state-r0.005"
+BATCH_WORKLOAD = "batched-64nets-n50-3000-omega256-4096-two-state-r0.005"
 PSI0 = 1024
 
 
@@ -49,6 +60,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mid", action="store_true",
+                    help="the single mid-size query (n = 100, 1024 chains) as the bench line")
+    ap.add_argument("--mid-steps", type=int, default=40, help="mid-size queries timed for the default line's mid_query")
     ap.add_argument("--sim-only", choices=["mid", "large", "wide"], default=None,
                     help="time the simulation kernel alone on a workload (kernel benchmark / profiling case)")
     ap.add_argument("--sim-steps", type=int, default=1024, help="transitions per launch in --sim-only")
@@ -78,7 +92,7 @@ def parse():
     ap.add_argument("--multi", type=int, default=0,
                     help="Q properties from the same trajectories against Q separate queries (mid workload)")
     ap.add_argument("--rates", default="50,200,1000,2000", help="arrival rates (queries/s) for --serve")
-    ap.add_argument("--queries", type=int, default=120, help="queries per rate for --serve")
+    ap.add_argument("--queries", type=int, default=1000, help="queries per rate for --serve")
     ap.add_argument("--max-length", type=int, default=1 << 20)
     return ap.parse_args()
 
@@ -295,43 +309,50 @@ def dist_setup():
 
 
 def run_reference(args):
+    """The oracle (single-threaded C) on bounded samples of the batched
+    workload: each step advances all chains of all 64 networks by T
+    transitions, T sized so that the whole run takes about two minutes."""
     world, rank, local = dist_setup()
     if rank != 0:
         return
     import oracle
     oracle.build()
-    net, soi, cfg = workload()
-    omega = cfg["omega"]
-    # one step = the oracle simulating all chains for a fixed number of
-    # transitions: about 2 minutes of CPU work over the whole run, at most
-    # 4 s per step
-    per_step_s = min(4.0, 120.0 / max(args.steps, 1))
-    _, calib_steps, _ = oracle_sample(net, soi, omega, target_s=0.5)
-    steps_per = max(2, int(calib_steps * per_step_s / 0.5))
-    st = oracle.init_states(net, 7, omega)
+    cfgs = batch_workload()
+    per_step_s = min(4.0, 120.0 / max(args.steps + args.warmup, 1))
+    rate, _, _ = oracle_batch_sample(cfgs, target_s=1.0)
+    work = sum(net.n * c["omega"] for net, _, c in cfgs)
+    T = max(1, int(per_step_s * rate / work))
+    states = [oracle.init_states(net, 7, c["omega"]) for net, _, c in cfgs]
     t0 = 0
+
+    def step():
+        nonlocal t0
+        for i, (net, soi, c) in enumerate(cfgs):
+            states[i], _ = oracle.simulate(net, 0, 7, states[i], t0, T, soi)
+        t0 += T
+
     for _ in range(args.warmup):
-        st, _ = oracle.simulate(net, 0, 7, st, t0, 2, soi)
-        t0 += 2
+        step()
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        st, _ = oracle.simulate(net, 0, 7, st, t0, steps_per, soi)
+        step()
         times.append(time.perf_counter() - t)
-        t0 += steps_per
-    upd = omega * steps_per * net.n
+    upd = work * T
     value = upd * len(times) / sum(times)
-    sample = f"oracle simulation of all {omega} chains for {steps_per} transitions per step"
+    sample = f"oracle simulation of all chains of all {len(cfgs)} networks for {T} transitions per step"
     line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": config_dict(cfg, net), "impl": "reference",
+            "config": batch_config_dict(cfgs), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def run_ours(args):
+def run_mid(args):
+    """The mid-size query as the bench line (--mid): n = 100, 1024 chains,
+    Alg. GR + Alg. 3 at r = 0.005, one query per step."""
     import torch
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -465,6 +486,299 @@ def run_ours(args):
         line["cpu_baseline_all_cores"] = {"value": va, "unit": "updates/s", "cores": cores, "kind": "oracle",
                                           "sample": f"{cores} processes, {omega_w} chains each, {steps_a} "
                                                     f"transitions ({dta:.1f} s)"}
+    print(json.dumps(line))
+
+
+def batch_workload():
+    import pbn_synth as S
+    return S.batch_configs()
+
+
+def batch_config_dict(cfgs):
+    ns = [int(net.n) for net, _, _ in cfgs]
+    oms = [int(c["omega"]) for _, _, c in cfgs]
+    return {"workload": BATCH_WORKLOAD, "networks": len(cfgs), "nodes": f"log-uniform [50, 3000] ({min(ns)}-{max(ns)})",
+            "chains": f"log-uniform [256, 4096] ({min(oms)}-{max(oms)})", "functions_per_node": 2,
+            "parents": "2-5", "p": "0.001 or 0.01", "rhat_threshold": 1.05, "r": 0.005, "s": 0.95, "eps": 1e-10,
+            "psi0": PSI0, "state_of_interest": "5 random nodes and values per network", "perturbation": "per-node",
+            "total_nodes": int(sum(ns)), "total_chains": int(sum(oms)),
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+def _batch_kw(c, seed, max_length):
+    return dict(omega=c["omega"], seed=seed, psi0=PSI0, rhat=c["rhat"], eps=c["eps"], r=c["r"], s=c["s"],
+                max_length=max_length)
+
+
+def oracle_batch_sample(cfgs, target_s=12.0):
+    """Times the oracle on a bounded sample of the batched workload: all
+    chains of all 64 networks advanced by T transitions each, T calibrated to
+    about target_s seconds.  Returns (updates/s, T, seconds)."""
+    import oracle
+    oracle.build()
+    states = [oracle.init_states(net, 99, c["omega"]) for net, _, c in cfgs]
+    t = time.perf_counter()
+    for (net, soi, c), st in zip(cfgs, states):
+        oracle.simulate(net, 0, 99, st, 0, 1, soi)
+    per = time.perf_counter() - t
+    T = max(1, int(round(target_s / max(per, 1e-6))))
+    t = time.perf_counter()
+    upd = 0
+    for (net, soi, c), st in zip(cfgs, states):
+        oracle.simulate(net, 0, 99, st, 1, T, soi)
+        upd += c["omega"] * T * net.n
+    dt = time.perf_counter() - t
+    return upd / dt, T, dt
+
+
+def _oracle_batch_worker(job):
+    """One host process of oracle_batch_all_cores: its networks' chains for T
+    transitions; returns (updates, seconds)."""
+    items, T = job
+    import oracle
+    t = time.perf_counter()
+    upd = 0
+    for net, soi, omega in items:
+        st = oracle.init_states(net, 99, omega)
+        oracle.simulate(net, 0, 99, st, 0, T, soi)
+        upd += omega * T * net.n
+    return upd, time.perf_counter() - t
+
+
+def oracle_batch_all_cores(cfgs, rate_one_core, target_s=8.0):
+    """The same oracle on every host core at once: the 64 networks dealt
+    over os.cpu_count() spawned processes (largest first, to the least
+    loaded), T transitions each, sized to about target_s seconds.
+    Throughput = all updates / the slowest process."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    work = sorted(((net.n * c["omega"], net, soi, c["omega"]) for net, soi, c in cfgs), key=lambda x: -x[0])
+    total = sum(w for w, *_ in work)
+    T = max(1, int(target_s * rate_one_core * cores / max(total, 1)))
+    bins = [[] for _ in range(cores)]
+    load = [0] * cores
+    for w, net, soi, om in work:
+        k = int(np.argmin(load))
+        bins[k].append((net, soi, om))
+        load[k] += w
+    jobs = [(b, T) for b in bins if b]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_batch_worker, jobs)
+    upd = sum(u for u, _ in res)
+    slowest = max(t for _, t in res)
+    return upd / slowest, len(jobs), T, slowest
+
+
+def measure_mid(P, torch, steps, warmup, seed0, flush):
+    """The mid-size query (n = 100, 1024 chains, two-state r = 0.005), one
+    query per step, CUDA events around each: throughput and latency."""
+    net, soi, cfg = workload()
+    N = P.pbn_load(net)
+    q = dict(omega=cfg["omega"], psi0=PSI0, rhat=cfg["rhat"], eps=cfg["eps"], r=cfg["r"], s=cfg["s"])
+    stream = torch.cuda.current_stream()
+    for w in range(warmup):
+        P.pbn_estimate_two_state(N, soi, seed=seed0 + 900_000 + w, **q)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times, upd, apply_ms, apply_launches, items = [], 0, 0.0, 0, 0
+    for k in range(steps):
+        flush.zero_()
+        ev0.record(stream)
+        rep = P.pbn_estimate_two_state(N, soi, seed=seed0 + k, **q)
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        upd += rep["chain_node_updates"]
+        apply_ms += rep["apply_ms"]
+        apply_launches += rep["apply_launches"]
+        items += rep["sim_items"]
+    N.close()
+    out = {"workload": WORKLOAD, "value": upd / (sum(times) / 1e3), "unit": "updates/s", "steps": steps,
+           "latency_ms": _percentiles(times)}
+    if apply_launches:
+        ops = float(apply_ops_per_item(net).sum()) * items / net.n
+        out["apply_resident_kernel_tops"] = ops / (apply_ms / 1e3) / 1e12
+    return out
+
+
+def run_ours(args):
+    """The default line: the batched workload, engine against the plain loop."""
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+
+    cfgs = batch_workload()
+    nets = [P.pbn_load(net) for net, _, _ in cfgs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    seed_base = 1_000_000 * (rank + 1)
+    seed_of = lambda step, k: seed_base + 1000 * step + k
+    ml = args.max_length
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    eng = P.Engine(use_graph=True)
+
+    def batched_step(step, networks=None):
+        """All 64 queries through the engine; returns (updates, per-query
+        latencies in ms, engine stats summed, reports by tag)."""
+        networks = networks or nets
+        t0 = time.perf_counter()
+        for k, ((net, soi, c), N) in enumerate(zip(cfgs, networks)):
+            eng.submit_two_state(N, soi, tag=k, **_batch_kw(c, seed_of(step, k), ml))
+        agg = {"epochs": 0, "sim_ms": 0.0, "sim_items": 0, "launches": 0, "d2h": 0, "epoch_ms": 0.0}
+        lat, reps = [], {}
+        while True:
+            st = eng.step()
+            agg["epochs"] += 1
+            agg["sim_ms"] += st["sim_ms"]
+            agg["sim_items"] += st["sim_items"]
+            agg["launches"] += st["kernel_launches"]
+            agg["d2h"] += st["d2h_bytes"]
+            agg["epoch_ms"] += st["epoch_ms"]
+            for r in eng.poll():
+                lat.append(1e3 * (time.perf_counter() - t0))
+                reps[r["tag"]] = r
+            if st["active"] == 0 and st["pending"] == 0:
+                break
+        bad = [k for k, r in reps.items() if r["status"] != 0]
+        if bad or len(reps) != len(cfgs):
+            raise RuntimeError(f"batched step {step}: queries {bad} failed or missing")
+        upd = sum(r["report"]["chain_node_updates"] for r in reps.values())
+        return upd, lat, agg, reps, st
+
+    def plain_step(step):
+        t0 = time.perf_counter()
+        lat, upd, launches = [], 0, 0
+        for k, ((net, soi, c), N) in enumerate(zip(cfgs, nets)):
+            r = P.pbn_estimate_two_state(N, soi, **_batch_kw(c, seed_of(step, k), ml))
+            upd += r["chain_node_updates"]
+            launches += r["kernel_launches"]
+            lat.append(1e3 * (time.perf_counter() - t0))
+        return upd, lat, launches
+
+    def timed(fn, *a):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        out = fn(*a)
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1), out
+
+    clocks = ClockSampler(local)
+    clocks.start()  # sampling runs before the timed region begins
+    for w in range(args.warmup):
+        batched_step(10_000 + w)
+        plain_step(10_000 + w)
+    barrier()
+    clocks.mark_begin()
+    b_ms, b_upd, b_lat, b_launch = [], 0, [], 0
+    sim_ms, ops, sim_items, epochs, epoch_ms = 0.0, 0.0, 0, 0, 0.0
+    ops_per_item = [float(algorithmic_ops_per_item(net).sum()) / net.n for net, _, _ in cfgs]
+    for k in range(args.steps):
+        ms, (upd, lat, agg, reps, st) = timed(batched_step, k)
+        b_ms.append(ms)
+        b_upd += upd
+        b_lat += lat
+        b_launch += agg["launches"]
+        sim_ms += agg["sim_ms"]
+        sim_items += agg["sim_items"]
+        epochs += agg["epochs"]
+        epoch_ms += agg["epoch_ms"]
+        ops += sum(ops_per_item[t] * r["report"]["sim_items"] for t, r in reps.items())
+    tuned = {key: st[key] for key in ("steps_per_epoch", "threads_per_block", "items_per_thread")}
+    p_ms, p_upd, p_lat, p_launch = [], 0, [], 0
+    for k in range(args.steps):
+        ms, (upd, lat, launches) = timed(plain_step, k)
+        p_ms.append(ms)
+        p_upd += upd
+        p_lat += lat
+        p_launch += launches
+    barrier()
+    clocks.mark_end()
+    clk = clocks.stop()
+
+    # e2e: the 64 networks' CSR arrays in pinned host memory, staged on the
+    # device inside the timed region; results read on the host
+    host = []
+    h2d = 0
+    for net, _, _ in cfgs:
+        arr = {key: torch.from_numpy(np.ascontiguousarray(getattr(net, key))).pin_memory()
+               for key in ("fn_offset", "par_offset", "parents", "truth_table", "select_prob")}
+        h2d += int(sum(v.numel() * v.element_size() for v in arr.values()))
+        host.append((arr, net.n, net.p))
+    e2e_s, e2e_upd, e2e_d2h = 0.0, 0, 0
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        staged = [P.pbn_load_pinned(a, n, pp) for a, n, pp in host]
+        upd, lat, agg, reps, _ = batched_step(k, staged)
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t
+        e2e_upd += upd
+        e2e_d2h += agg["d2h"]
+        for Nk in staged:
+            Nk.close()
+    barrier()
+    eng.close()
+
+    total_ms, plain_ms = sum(b_ms), sum(p_ms)
+    (total_ms, plain_ms, e2e_s), (upd_all, p_upd_all, e2e_upd_all) = reduce_over_ranks(
+        [total_ms, plain_ms, e2e_s], [b_upd, p_upd, e2e_upd], world, "cuda")
+    if rank != 0:
+        return
+    value = upd_all / (total_ms / 1e3)
+    plain_value = p_upd_all / (plain_ms / 1e3)
+    peak, sms, mhz, peak_src = alu_peak_tops(local)
+    achieved = ops / (sim_ms / 1e3) / 1e12 if sim_ms > 0 else None
+    line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": batch_config_dict(cfgs),
+            "latency_ms": _percentiles(b_lat),
+            "queries_per_s": len(cfgs) * args.steps * world / (total_ms / 1e3),
+            "plain": {"value": plain_value, "unit": "updates/s", "ms_per_step": plain_ms / args.steps,
+                      "latency_ms": _percentiles(p_lat),
+                      "queries_per_s": len(cfgs) * args.steps * world / (plain_ms / 1e3),
+                      "form": "one pbn_estimate_two_state per network, in order", "gpu_launches": p_launch},
+            "speedup_vs_plain": value / plain_value, "same_updates": b_upd == p_upd,
+            "engine": {"epochs_per_step": epochs / args.steps, "tuned": tuned,
+                       "device_ms_per_step": epoch_ms / args.steps},
+            "roofline": {"bound": "alu", "kernel": "batch_sim_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "Tops/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "peak_source": f"issue rate {sms} SMs x 128 lanes x {mhz:.0f} MHz ({peak_src})",
+                         "kernel_share_of_step": sim_ms / total_ms,
+                         "launches": epochs, "avg_launch_ms": sim_ms / max(epochs, 1),
+                         "ops_per_update": ops / max(sim_items, 1) / 32,
+                         "items_per_launch": sim_items / max(epochs, 1)},
+            "clocks": clk,
+            "e2e": {"value": e2e_upd_all / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": e2e_d2h // max(args.steps, 1)},
+            "gpu_launches": int(b_launch)}
+    if world == 1:
+        line["mid_query"] = measure_mid(P, torch, args.mid_steps, 3, 5_000_000, flush)
+    if world == 1 and not args.no_cpu_baseline:
+        v, T, dt = oracle_batch_sample(cfgs)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                                "sample": f"oracle simulation of all chains of all {len(cfgs)} networks for {T} "
+                                          f"transitions ({dt:.1f} s)"}
+        va, procs, Ta, dta = oracle_batch_all_cores(cfgs, v)
+        line["cpu_baseline_all_cores"] = {"value": va, "unit": "updates/s", "cores": procs, "kind": "oracle",
+                                          "sample": f"{procs} processes, the networks dealt between them, {Ta} "
+                                                    f"transitions each ({dta:.1f} s)"}
     print(json.dumps(line))
 
 
@@ -764,8 +1078,9 @@ def run_sweep(args):
 def run_serve(args):
     """Serving: queries arrive as a Poisson process; each names a random
     network of the 200-network pool (n log-uniform in [20, 3000]), a state
-    of interest of 1-10 nodes and r in {0.01, 0.005, 0.001} (two-state, 1024
-    chains).  The engine admits them while others run (continuous batching);
+    of interest of 1-10 nodes, r in {0.01, 0.005, 0.001} and the two-state or
+    the Skart stopping rule (half each; Skart at absolute precision r), 1024
+    chains.  The engine admits them while others run (continuous batching);
     the baseline serves the same arrival trace one query at a time."""
     import torch
     import pbn_synth as S
@@ -777,12 +1092,36 @@ def run_serve(args):
     nets = [P.pbn_load(n) for n in pool]
     rng = np.random.default_rng(1508078284)
     out = {"mode": "serve", "pool": len(pool), "queries_per_rate": args.queries, "rates": []}
+
+    def submit(eng, q, tag):
+        i, soi, r, seed, kind = q
+        kw = dict(omega=1024, seed=seed, psi0=PSI0, rhat=1.05, max_length=args.max_length, tag=tag)
+        if kind == "ts":
+            eng.submit_two_state(nets[i], soi, r=r, **kw)
+        else:
+            eng.submit_skart(nets[i], soi, H_star=r, relative=False, alpha=0.05, **kw)
+
+    def alone(q):
+        i, soi, r, seed, kind = q
+        kw = dict(omega=1024, seed=seed, psi0=PSI0, rhat=1.05, max_length=args.max_length)
+        if kind == "ts":
+            return P.pbn_estimate_two_state(nets[i], soi, r=r, **kw)
+        return P.pbn_estimate_skart(nets[i], soi, H_star=r, relative=False, alpha=0.05, **kw)
+
+    # the engine's autotuner settles on a short warm-up trace
+    eng = P.Engine(use_graph=True)
+    for k in range(16):
+        i = int(rng.integers(len(pool)))
+        submit(eng, (i, S.random_soi(rng, pool[i].n), 0.01, 5000 + k, "ts" if k % 2 else "sk"), k)
+    eng.run()
+    eng.close()
     for rate in [float(x) for x in args.rates.split(",")]:
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.queries))
         qs = []
         for k in range(args.queries):
             i = int(rng.integers(len(pool)))
-            qs.append((i, S.random_soi(rng, pool[i].n), float(rng.choice([0.01, 0.005, 0.001])), 10_000 + k))
+            qs.append((i, S.random_soi(rng, pool[i].n), float(rng.choice([0.01, 0.005, 0.001])), 10_000 + k,
+                       "ts" if rng.random() < 0.5 else "sk"))
         # engine, continuous batching
         eng = P.Engine(use_graph=True)
         torch.cuda.synchronize()
@@ -791,14 +1130,13 @@ def run_serve(args):
         while done < len(qs):
             now = time.perf_counter() - t0
             while nxt < len(qs) and arrivals[nxt] <= now:
-                i, soi, r, seed = qs[nxt]
-                eng.submit_two_state(nets[i], soi, omega=1024, seed=seed, psi0=PSI0, rhat=1.05, r=r,
-                                     max_length=args.max_length, tag=nxt)
+                submit(eng, qs[nxt], nxt)
                 nxt += 1
             st = eng.step()
             for res in eng.poll():
                 lat.append(time.perf_counter() - t0 - arrivals[res["tag"]])
-                upd += res["report"]["chain_node_updates"]
+                rep = res["report"]
+                upd += rep["chain_node_updates"]
                 ok += res["status"] == 0
                 done += 1
             if st["active"] == 0 and st["pending"] == 0 and nxt < len(qs):
@@ -807,16 +1145,16 @@ def run_serve(args):
         eng.close()
         # baseline: the same trace served one query at a time
         t0 = time.perf_counter()
-        blat, bupd, free_at = [], 0, 0.0
-        for k, (i, soi, r, seed) in enumerate(qs):
+        blat, bupd, free_at, bok = [], 0, 0.0, 0
+        for k, q in enumerate(qs):
             start = max(free_at, arrivals[k])
             wait = start - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(wait)
             try:
-                rep = P.pbn_estimate_two_state(nets[i], soi, omega=1024, seed=seed, psi0=PSI0, rhat=1.05, r=r,
-                                               max_length=args.max_length)
+                rep = alone(q)
                 bupd += rep["chain_node_updates"]
+                bok += 1
             except P.PbnError:
                 pass
             free_at = time.perf_counter() - t0
@@ -826,7 +1164,8 @@ def run_serve(args):
                              "engine": {"latency_s": _percentiles(lat), "queries_per_s": len(qs) / wall,
                                         "updates_per_s": upd / wall, "ok": ok},
                              "one_at_a_time": {"latency_s": _percentiles(blat), "queries_per_s": len(qs) / bwall,
-                                               "updates_per_s": bupd / bwall}})
+                                               "updates_per_s": bupd / bwall, "ok": bok}})
+        print(json.dumps(out["rates"][-1]), file=sys.stderr, flush=True)
     print(json.dumps(out))
 
 
@@ -854,6 +1193,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.mid:
+        run_mid(args)
     else:
         run_ours(args)
 

@@ -50,7 +50,8 @@ typedef enum pbn_status {
     PBN_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up */
     PBN_ERR_NOT_CONVERGED = 5,  /* a stopping rule was not met within the length cap */
     PBN_ERR_INSUFFICIENT = 6,   /* the window cannot give alpha and beta (no 0->1 or 1->0) */
-    PBN_ERR_UNSUPPORTED = 7     /* valid input beyond this build's limits */
+    PBN_ERR_UNSUPPORTED = 7,    /* valid input beyond this build's limits */
+    PBN_ERR_CANCELLED = 8       /* an engine query withdrawn by pbn_engine_cancel */
 } pbn_status;
 
 enum { PBN_PERTURB_PER_NODE = 0, PBN_PERTURB_GLOBAL = 1 };
@@ -476,6 +477,9 @@ typedef struct pbn_engine_stats {
     int64_t hbm_in_use;
     int32_t steps_per_epoch, threads_per_block, items_per_thread;
     int32_t kernel_launches;           /* kernels this epoch launched */
+    double sim_ms;                     /* CUDA-event time of this epoch's batch_sim_kernel launch (0: none) */
+    int64_t sim_items;                 /* its (node, chain group, transition) items */
+    int64_t d2h_bytes;                 /* device -> host bytes this epoch read (results, status) */
 } pbn_engine_stats;
 
 /* Create an engine on the current device.  It runs on a stream of its own,
@@ -490,8 +494,19 @@ int pbn_engine_submit(pbn_engine *engine, const pbn_engine_query *query, int64_t
  * A query that fails ends with its status in the result; the call itself
  * fails only for engine-wide errors (PBN_ERR_CUDA, PBN_ERR_OOM). */
 int pbn_engine_step(pbn_engine *engine, pbn_engine_stats *stats);
-/* Move up to max_results finished results into out (host memory). */
+/* Move up to max_results finished results into out (host memory).  In a
+ * result, two_state.sim_items / skart.sim_items count the query's items
+ * simulated by the batched kernel (not those of epochs in which a lone query
+ * ran on the single-query schedule). */
 int pbn_engine_poll(pbn_engine *engine, pbn_engine_result *out, int32_t max_results, int32_t *count);
+/* Withdraw query `id` (waiting or active) between epochs, for a client that
+ * no longer wants its answer (a stopping rule that may never fire short of
+ * max_length, a deadline passed).  Its chain buffers are freed and its
+ * result is queued for pbn_engine_poll with status PBN_ERR_CANCELLED; the
+ * other queries are not affected (their results stay the same).
+ * Errors: PBN_ERR_INVALID (NULL engine, or no waiting or active query with
+ * that id: unknown, finished or already cancelled). */
+int pbn_engine_cancel(pbn_engine *engine, int64_t id);
 
 /* ---------------------------------------------------------------- errors */
 

@@ -29,6 +29,7 @@ PBN_ERR_TIMEOUT = 4
 PBN_ERR_NOT_CONVERGED = 5
 PBN_ERR_INSUFFICIENT = 6
 PBN_ERR_UNSUPPORTED = 7
+PBN_ERR_CANCELLED = 8
 PER_NODE = 0
 GLOBAL = 1
 MAX_SOI = 32
@@ -150,7 +151,8 @@ class EngineResult(ctypes.Structure):
 class EngineStats(ctypes.Structure):
     _fields_ = [("epoch", c_i64), ("active", c_i32), ("pending", c_i32), ("finished", c_i64), ("updates", c_i64),
                 ("epoch_ms", c_dbl), ("hbm_in_use", c_i64), ("steps_per_epoch", c_i32),
-                ("threads_per_block", c_i32), ("items_per_thread", c_i32), ("kernel_launches", c_i32)]
+                ("threads_per_block", c_i32), ("items_per_thread", c_i32), ("kernel_launches", c_i32),
+                ("sim_ms", c_dbl), ("sim_items", c_i64), ("d2h_bytes", c_i64)]
 
 
 METHOD_TWO_STATE = 0
@@ -193,6 +195,7 @@ def lib():
             L.pbn_engine_submit.argtypes = [c_vp, P(EngineQuery), P(c_i64)]
             L.pbn_engine_step.argtypes = [c_vp, P(EngineStats)]
             L.pbn_engine_poll.argtypes = [c_vp, c_vp, c_i32, P(c_i32)]
+            L.pbn_engine_cancel.argtypes = [c_vp, c_i64]
             L.pbn_take_device_status.argtypes = [P(c_i32)]
             L.pbn_last_error.restype = ctypes.c_char_p
             L.pbn_status_string.restype = ctypes.c_char_p
@@ -617,6 +620,11 @@ class Engine:
             self._nets.pop(r.id, None)
             out.append(d)
         return out
+
+    def cancel(self, qid: int) -> None:
+        """Withdraw a waiting or active query; its result arrives with status
+        PBN_ERR_CANCELLED."""
+        _check(lib().pbn_engine_cancel(self.handle, int(qid)))
 
     def run(self, max_epochs: int = 1_000_000) -> list:
         """Step until nothing is active or waiting; returns all results."""

@@ -654,6 +654,7 @@ const char *pbn_status_string(int status) {
     case PBN_ERR_NOT_CONVERGED: return "not converged within the length cap";
     case PBN_ERR_INSUFFICIENT: return "window cannot give alpha and beta";
     case PBN_ERR_UNSUPPORTED: return "unsupported by this build";
+    case PBN_ERR_CANCELLED: return "cancelled";
     default: return "unknown status";
   }
 }

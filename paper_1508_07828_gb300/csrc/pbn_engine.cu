@@ -256,6 +256,8 @@ struct EQuery {
   pbn_skart_report sr;
   int64_t submit_epoch = 0, admit_epoch = -1, finish_epoch = -1;
   int64_t updates = 0;
+  int64_t batch_items = 0;   // (node, group, transition) items of batch_sim_kernel launches
+  int64_t batch_items_epoch = 0;
 
   EQuery() {
     memset(&tsq, 0, sizeof tsq);
@@ -296,6 +298,7 @@ struct pbn_engine {
   StatsScratch sk;
   pbn_skart_result *d_sk = nullptr, *h_sk = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t es0 = nullptr, es1 = nullptr;  // around batch_sim_kernel (graph: external event nodes)
   cudaGraphExec_t exec = nullptr;
   int *status = nullptr;                 // device status word of the batched launches
   std::vector<EQuery *> epoch_queries;   // queries simulated in the current epoch
@@ -549,6 +552,8 @@ void retire(pbn_engine *e) {
     r.status = q.status;
     q.tr.chain_node_updates = q.updates;
     q.sr.chain_node_updates = q.updates;
+    q.tr.sim_items = q.batch_items;
+    q.sr.sim_items = q.batch_items;
     r.two_state = q.tr;
     r.skart = q.sr;
     r.submit_epoch = q.submit_epoch;
@@ -575,7 +580,10 @@ int capture_graph(pbn_engine *e, int threads, size_t smem) {
   cudaMemcpyAsync(e->d_items, e->h_items, sizeof(BatchItem) * e->max_items, cudaMemcpyHostToDevice, e->s);
   cudaMemcpyAsync(e->d_reqs, e->h_reqs, sizeof(StatReq) * e->cfg.max_active, cudaMemcpyHostToDevice, e->s);
   cudaMemcpyAsync(e->d_cnt, e->h_cnt, sizeof(int) * kCounters, cudaMemcpyHostToDevice, e->s);
+  // timing events of the simulation launch, kept in the graph as event nodes
+  cudaEventRecordWithFlags(e->es0, e->s, cudaEventRecordExternal);
   batch_sim_kernel<<<sim_blocks, threads, gsmem, e->s>>>(e->d_tasks, e->d_items, e->d_cnt);
+  cudaEventRecordWithFlags(e->es1, e->s, cudaEventRecordExternal);
   batch_stats_kernel<<<e->sms, 256, 0, e->s>>>(e->d_reqs, e->d_cnt, e->d_partials, e->d_tickets, e->d_out);
   cudaMemcpyAsync(e->h_out, e->d_out, sizeof(ReqOut) * e->cfg.max_active, cudaMemcpyDeviceToHost, e->s);
   ECUDA(cudaStreamEndCapture(e->s, &g), "end capture");
@@ -596,8 +604,10 @@ int launch_direct(pbn_engine *e, int threads, size_t smem, int ntask, int nitems
   if (nreq) ECUDA(cudaMemcpyAsync(e->d_reqs, e->h_reqs, sizeof(StatReq) * nreq, cudaMemcpyHostToDevice, e->s), "reqs");
   ECUDA(cudaMemcpyAsync(e->d_cnt, e->h_cnt, sizeof(int) * kCounters, cudaMemcpyHostToDevice, e->s), "counters");
   if (nitems) {
+    ECUDA(cudaEventRecord(e->es0, e->s), "event");
     batch_sim_kernel<<<sim_blocks, threads, smem, e->s>>>(e->d_tasks, e->d_items, e->d_cnt);
     ECUDA(cudaGetLastError(), "batch simulation launch");
+    ECUDA(cudaEventRecord(e->es1, e->s), "event");
   }
   if (nreq) {
     batch_stats_kernel<<<e->sms, 256, 0, e->s>>>(e->d_reqs, e->d_cnt, e->d_partials, e->d_tickets, e->d_out);
@@ -654,6 +664,8 @@ extern "C" int pbn_engine_create(const pbn_engine_cfg *cfg, void *stream, pbn_en
   ECUDA(cudaMallocHost(&e->h_sk, sizeof(pbn_skart_result)), "engine alloc");
   ECUDA(cudaEventCreate(&e->e0), "event");
   ECUDA(cudaEventCreate(&e->e1), "event");
+  ECUDA(cudaEventCreate(&e->es0), "event");
+  ECUDA(cudaEventCreate(&e->es1), "event");
   ECUDA(cudaMalloc(&e->status, sizeof(int)), "engine alloc");
   ECUDA(cudaMemsetAsync(e->status, 0, sizeof(int), e->s), "engine memset");
   memset(e->h_tasks, 0, sizeof(SimArgs) * A);
@@ -710,6 +722,7 @@ extern "C" void pbn_engine_destroy(pbn_engine *e) {
   scratch_free(e->sk);
   cudaFree(e->d_sk); cudaFreeHost(e->h_sk);
   cudaEventDestroy(e->e0); cudaEventDestroy(e->e1);
+  cudaEventDestroy(e->es0); cudaEventDestroy(e->es1);
   cudaFree(e->status);
   cudaStreamDestroy(e->s);
   delete e;
@@ -785,6 +798,7 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
     EQuery &q = *qp;
     q.sim_D = 0;
     q.req = -1;
+    q.batch_items_epoch = 0;
     if (q.phase == PH_DONE) continue;
     if (q.ch.length < q.target) {
       if (ntask >= e->cfg.max_active) continue;
@@ -834,6 +848,7 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       task_groups.push_back(std::make_pair(ntask, gpb));
       nitems += (int)groups_items;
       q.sim_D = D;
+      q.batch_items_epoch = (int64_t)d.n * q.G * D;
       updates += q.omega * D * d.n;
       q.updates += q.omega * D * d.n;
       ntask++;
@@ -908,20 +923,31 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
   e->h_cnt[2] = vblocks;
   e->h_cnt[3] = 0;
   e->h_cnt[4] = nreq;
+  int64_t d2h = sizeof(int);  // the status word
   if (nitems || nreq) {
     if (e->cfg.use_graph) {
       if ((rc = capture_graph(e, cand.threads, smem))) return rc;
       ECUDA(cudaGraphLaunch(e->exec, e->s), "graph launch");
       launches += 2;
+      d2h += (int64_t)sizeof(ReqOut) * e->cfg.max_active;
     } else {
       if ((rc = launch_direct(e, cand.threads, smem, ntask, nitems, nreq))) return rc;
       launches += (nitems ? 1 : 0) + (nreq ? 1 : 0);
+      if (nreq) d2h += (int64_t)sizeof(ReqOut) * nreq;
     }
   }
   ECUDA(cudaEventRecord(e->e1, e->s), "event");
   ECUDA(cudaStreamSynchronize(e->s), "epoch sync");
-  float ms = 0.f;
+  float ms = 0.f, sim_ms = 0.f;
   cudaEventElapsedTime(&ms, e->e0, e->e1);
+  int64_t sim_items = 0;
+  if (nitems) {
+    cudaEventElapsedTime(&sim_ms, e->es0, e->es1);
+    for (EQuery *q : e->epoch_queries) {
+      q->batch_items += q->batch_items_epoch;
+      sim_items += q->batch_items_epoch;
+    }
+  }
   {
     // a bounded device wait that gave up fails every query of this epoch
     int stv = 0;
@@ -952,6 +978,7 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
     if ((q.phase == PH_SK_SKEW || q.phase == PH_SK_RAND || q.phase == PH_SK_CI) && q.ch.length >= q.target) {
       if ((rc = skart_check(e, q))) return rc;
       launches += 2;
+      d2h += sizeof(pbn_skart_result);
     }
   }
   if (e->best < 0 && updates > 0 && !alone) {
@@ -987,8 +1014,35 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
     st->threads_per_block = cand.threads;
     st->items_per_thread = cand.ipt;
     st->kernel_launches = launches;
+    st->sim_ms = sim_ms;
+    st->sim_items = sim_items;
+    st->d2h_bytes = d2h;
   }
   return PBN_OK;
+}
+
+extern "C" int pbn_engine_cancel(pbn_engine *e, int64_t id) {
+  if (!e) return efail(PBN_ERR_INVALID, "NULL engine");
+  // no work is in flight between calls (pbn_engine_step synchronises), so a
+  // cancelled query's buffers can be released at once
+  for (auto it = e->pending.begin(); it != e->pending.end(); ++it) {
+    if ((*it)->id != id) continue;
+    EQuery &q = **it;
+    q.status = PBN_ERR_CANCELLED;
+    q.phase = PH_DONE;
+    q.finish_epoch = e->epoch;
+    e->active.push_back(std::move(*it));
+    e->pending.erase(it);
+    retire(e);
+    return PBN_OK;
+  }
+  for (auto &qp : e->active) {
+    if (qp->id != id || qp->phase == PH_DONE) continue;
+    finish(e, *qp, PBN_ERR_CANCELLED);
+    retire(e);
+    return PBN_OK;
+  }
+  return efail(PBN_ERR_INVALID, "no waiting or active query %lld", (long long)id);
 }
 
 extern "C" int pbn_engine_poll(pbn_engine *e, pbn_engine_result *out, int32_t max_results, int32_t *count) {

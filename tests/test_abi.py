@@ -42,6 +42,11 @@ def test_status_strings_and_error_channel():
     # NULL arguments are rejected on the host without touching the device
     assert lib.pbn_load(None, None) == 1
     assert b"NULL" in lib.pbn_last_error()
+    assert lib.pbn_status_string(8) == b"cancelled"
+    # cancelling on no engine is refused on the host
+    lib.pbn_engine_cancel.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert lib.pbn_engine_cancel(None, 3) == 1
+    assert b"NULL" in lib.pbn_last_error()
 
 
 STRUCTS = {
@@ -84,7 +89,7 @@ STRUCTS = {
                                            "admit_epoch", "finish_epoch"]),
     "EngineStats": ("pbn_engine_stats", ["epoch", "active", "pending", "finished", "updates", "epoch_ms",
                                          "hbm_in_use", "steps_per_epoch", "threads_per_block", "items_per_thread",
-                                         "kernel_launches"]),
+                                         "kernel_launches", "sim_ms", "sim_items", "d2h_bytes"]),
 }
 
 

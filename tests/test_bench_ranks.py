@@ -1,5 +1,5 @@
 """The multi-replica path of bench.py on CPU: two gloo ranks (127.0.0.1).
-bench.py --gpus N runs N independent replicas of the query stream (the
+bench.py --gpus N runs N independent replicas of the batched workload (the
 queries shard with no exchange); the only cross-rank step is the whole-job
 reduction of the timed region (slowest rank) and of the work (sum), which
 runs here on gloo exactly as it runs on NCCL; and the reference arm runs on
@@ -90,5 +90,5 @@ def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    net, _, cfg = bench.workload()
-    assert d["config"] == bench.config_dict(cfg, net)
+    assert d["config"] == bench.batch_config_dict(bench.batch_workload())
+    assert d["config"]["workload"] == bench.BATCH_WORKLOAD

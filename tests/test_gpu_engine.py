@@ -151,3 +151,215 @@ def test_failed_query_reports_status_and_others_finish(P, alone):
     badr = [r for r in res if r["tag"] == 999]
     assert badr and badr[0]["status"] == P.PBN_ERR_NOT_CONVERGED
     _check([r for r in res if r["tag"] != 999], alone)
+
+
+# ------------------------------------------------------- against the oracle
+
+import oracle  # noqa: E402
+
+
+def _oracle_of(kind, net, soi, kw):
+    kw = dict(kw)
+    if kind == "ts":
+        return oracle.estimate_two_state(net, soi, **kw)
+    return oracle.estimate_skart(net, soi, alpha=0.05, **kw)
+
+
+def _cmp_oracle(kind, g, o, what):
+    """Engine report vs oracle run of the same query: integer decisions and
+    counts exactly, FP64 statistics as the single-query parity tests do."""
+    assert o["status"] == 0, (what, o)
+    if kind == "ts":
+        for k in ("psi", "gr_psi", "length", "sample_size", "ones", "gr_rounds", "ts_rounds", "M", "N"):
+            assert g[k] == o[k], (what, k, g[k], o[k])
+        assert list(g["n4"]) == list(o["n4"]), what
+        assert g["prob"] == o["prob"] and g["alpha"] == o["alpha"] and g["beta"] == o["beta"], what
+        assert g["rhat"] == pytest.approx(o["rhat"], rel=1e-12), what
+    else:
+        for k in ("psi", "length", "kappa", "batches", "spacer", "sample_size", "gr_rounds", "rand_rounds",
+                  "ci_rounds"):
+            assert g[k] == o[k], (what, k, g[k], o[k])
+        for k in ("mean", "ci_lo", "ci_hi", "H", "var", "skew", "phi"):
+            assert g[k] == pytest.approx(o[k], rel=1e-10, abs=1e-13), (what, k)
+
+
+def test_mix_matches_oracle(P):
+    """Every query of the mix whose network the oracle simulates in seconds,
+    compared field by field with the oracle's own Alg. GR + Alg. 3 / Alg. 4
+    (not with the single-query GPU driver), after running in the mix."""
+    eng = P.Engine(use_graph=True)
+    nets = {}
+    for i in range(len(QUERIES)):
+        _submit(P, eng, i, nets)
+    res = {r["tag"]: r for r in eng.run()}
+    checked = 0
+    for i, (kind, net, soi, kw) in enumerate(QUERIES):
+        if net.n * kw["omega"] > 200_000:
+            continue
+        assert res[i]["status"] == 0
+        _cmp_oracle(kind, res[i]["report"], _oracle_of(kind, net, soi, kw), (i, net.name))
+        checked += 1
+    assert checked >= 8
+
+
+def test_cancel_pending_and_active(P, alone):
+    """A withdrawn query reports PBN_ERR_CANCELLED and frees its slot; the
+    other queries' results do not change."""
+    eng = P.Engine(max_active=3, steps_per_epoch=256)
+    nets = {}
+    ids = [_submit(P, eng, i, nets) for i in range(len(QUERIES))]
+    eng.cancel(ids[-1])                       # still waiting (3 slots)
+    st = eng.step()
+    assert st["active"] >= 1
+    eng.cancel(ids[0])                        # admitted in the first epoch
+    with pytest.raises(P.PbnError) as e:
+        eng.cancel(ids[0])                    # already cancelled
+    assert e.value.status == P.PBN_ERR_INVALID
+    with pytest.raises(P.PbnError):
+        eng.cancel(10_000)                    # unknown id
+    res = eng.poll() + eng.run()
+    cancelled = [r for r in res if r["status"] == P.PBN_ERR_CANCELLED]
+    assert sorted(r["tag"] for r in cancelled) == [0, len(QUERIES) - 1]
+    for r in res:
+        if r["status"] == P.PBN_ERR_CANCELLED:
+            continue
+        assert r["status"] == 0
+        ref = alone[r["tag"]]
+        keys = TS_KEYS if QUERIES[r["tag"]][0] == "ts" else SK_KEYS
+        for k in keys:
+            assert r["report"][k] == ref[k], (r["tag"], k)
+    assert len(res) == len(QUERIES)
+    with pytest.raises(P.PbnError):
+        eng.cancel(ids[1])                    # finished
+
+
+# ------------------------------------------- the batched workload (64 networks)
+
+def _replay_window(P, net, soi, omega, seed, rep, rng, mode=0):
+    """Replays the query's chains to its final length with pbn_run_chains and
+    recounts the window [psi, length) on the host; sampled chains are
+    replayed by the oracle, bit for bit."""
+    N = P.pbn_load(net)
+    L, psi = rep["length"], rep["psi"]
+    cs = P.ChainSet(N, omega, bits_cap=L)
+    P.pbn_init_chains(cs, seed, mode)
+    P.pbn_run_chains(cs, L, seed, mode, soi)
+    x = cs.indicator_numpy(psi, L - psi)
+    assert int(x.sum()) == rep["ones"]
+    a, b = x[:, :-1], x[:, 1:]
+    n4 = [int(((a == i) & (b == j)).sum()) for i in (0, 1) for j in (0, 1)]
+    assert n4 == list(rep["n4"])
+    states = cs.states_numpy()
+    for c in sorted({0, omega - 1, int(rng.integers(omega))}):
+        st0 = oracle.init_states(net, seed, 1, chain0=c)
+        ref, ind = oracle.simulate(net, mode, seed, st0, 0, L, soi, chain0=c)
+        assert np.array_equal(states[c], ref[0]), c
+        assert np.array_equal(x[c], ind[0][psi:]), c
+
+
+def test_batch_workload_in_mix_equals_alone_and_replays():
+    """The batched workload's 64 networks (n log-uniform in [50, 3000],
+    256-4096 chains, p in {0.001, 0.01}, two-state r = 0.005) in one engine:
+    every query equals its single-query run; for the networks of n >= 2000
+    the chains replayed to the query's final length give its counts, and
+    sampled chains match the oracle."""
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+    cfgs = S.batch_configs()
+    assert len(cfgs) == 64 and max(net.n for net, _, _ in cfgs) >= 2000
+    nets = [P.pbn_load(net) for net, _, _ in cfgs]
+    kw = lambda c, k: dict(omega=c["omega"], seed=1000 + k, psi0=1024, rhat=c["rhat"], eps=c["eps"], r=c["r"],
+                           s=c["s"], max_length=1 << 20)
+    eng = P.Engine(use_graph=True)
+    for k, ((net, soi, c), N) in enumerate(zip(cfgs, nets)):
+        eng.submit_two_state(N, soi, tag=k, **kw(c, k))
+    res = {r["tag"]: r for r in eng.run()}
+    assert len(res) == 64
+    rng = np.random.default_rng(5)
+    replayed = 0
+    for k, ((net, soi, c), N) in enumerate(zip(cfgs, nets)):
+        ref = P.pbn_estimate_two_state(N, soi, **kw(c, k))
+        got = res[k]
+        assert got["status"] == 0
+        for key in TS_KEYS:
+            assert got["report"][key] == ref[key], (k, key)
+        if net.n >= 2000:
+            _replay_window(P, net, soi, c["omega"], 1000 + k, got["report"], rng)
+            replayed += 1
+    assert replayed >= 2
+
+
+# ----------------------------------------------- the serving pool (200 networks)
+
+def _serving_queries(count=40, seed=1508078290):
+    pool = S.serving_pool()
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        i = int(rng.integers(len(pool)))
+        soi = S.random_soi(rng, pool[i].n)
+        r = float(rng.choice([0.01, 0.005, 0.001]))
+        kind = "ts" if k % 2 == 0 else "sk"
+        out.append((kind, i, soi, r, 20_000 + k))
+    return pool, out
+
+
+def test_serving_pool_continuous_mix():
+    """Queries over the 200-network serving pool (n log-uniform in [20, 3000],
+    1-10-node states of interest, r in {0.01, 0.005, 0.001}, two-state and
+    Skart at absolute precision r), submitted a few per epoch while others
+    run: each result equals the query alone; the queries on small networks
+    also equal the oracle's."""
+    from paper_1508_07828_gb300 import _build
+    _build.build()
+    import paper_1508_07828_gb300 as P
+    pool, qs = _serving_queries()
+    loaded = {}
+
+    def net_of(i):
+        if i not in loaded:
+            loaded[i] = P.pbn_load(pool[i])
+        return loaded[i]
+
+    def kwargs(kind, r, seed):
+        base = dict(omega=256, seed=seed, psi0=512, rhat=1.05, max_length=1 << 15)
+        if kind == "ts":
+            return dict(base, r=r)
+        return dict(base, H_star=r, relative=False)
+
+    eng = P.Engine(use_graph=True)
+    results, nxt = [], 0
+    for _ in range(100_000):
+        for _ in range(3):
+            if nxt < len(qs):
+                kind, i, soi, r, seed = qs[nxt]
+                if kind == "ts":
+                    eng.submit_two_state(net_of(i), soi, tag=nxt, **kwargs(kind, r, seed))
+                else:
+                    eng.submit_skart(net_of(i), soi, alpha=0.05, tag=nxt, **kwargs(kind, r, seed))
+                nxt += 1
+        st = eng.step()
+        results += eng.poll()
+        if nxt == len(qs) and st["active"] == 0 and st["pending"] == 0:
+            break
+    assert len(results) == len(qs)
+    oracle_checked = 0
+    for res in results:
+        kind, i, soi, r, seed = qs[res["tag"]]
+        kw = kwargs(kind, r, seed)
+        try:
+            ref = (P.pbn_estimate_two_state(net_of(i), soi, **kw) if kind == "ts"
+                   else P.pbn_estimate_skart(net_of(i), soi, alpha=0.05, **kw))
+            ref_status = 0
+        except P.PbnError as e:
+            ref, ref_status = None, e.status
+        assert res["status"] == ref_status, (res["tag"], res["status"], ref_status)
+        if ref is None:
+            continue
+        for key in (TS_KEYS if kind == "ts" else SK_KEYS):
+            assert res["report"][key] == ref[key], (res["tag"], key)
+        if pool[i].n <= 60 and res["report"]["length"] * pool[i].n <= 3_000_000:
+            _cmp_oracle(kind, res["report"], _oracle_of(kind, pool[i], soi, kw), res["tag"])
+            oracle_checked += 1
+    assert oracle_checked >= 2

@@ -271,17 +271,42 @@ def test_estimate_two_state_matches_oracle(P, case):
         _cmp_two_state(g, o)
 
 
-@pytest.mark.parametrize("case", ["identity", "tiny"])
+@pytest.mark.parametrize("case", ["identity", "tiny", "mid-relative", "tiny-multibatch", "three-node-multibatch",
+                                  "identity-correlated"])
 def test_estimate_skart_matches_oracle(P, case):
+    """Alg. GR + Alg. 4 end to end, GPU vs oracle: every decision (kappa, the
+    batch count, the spacer, the rounds of each loop) and length exactly, the
+    FP64 statistics to 1e-10 relative.  The multi-batch cases keep omega small
+    (80 or more batches per chain), so the randomness test on within-chain
+    spaced batch means and the lag-1 correlation act on real data."""
     if case == "identity":
         net, soi, kw = S.identity_node(0.2), S.StateOfInterest([0], [1]), dict(omega=16, psi0=256, rhat=1.1,
                                                                               H_star=0.05, relative=True)
-    else:
+    elif case == "tiny":
         net, soi, _ = S.tiny_config()
         soi = S.StateOfInterest([3], [1])
         kw = dict(omega=8, psi0=1024, rhat=1.1, H_star=0.01, relative=False)
+    elif case == "mid-relative":
+        net, soi, _ = S.mid_config()
+        kw = dict(omega=1024, psi0=1024, rhat=1.05, H_star=0.05, relative=True)
+    elif case == "tiny-multibatch":
+        net, soi, _ = S.tiny_config()
+        kw = dict(omega=16, psi0=512, rhat=1.1, H_star=0.004, relative=False)
+    elif case == "three-node-multibatch":
+        net, soi = S.three_node(1 / 16), S.StateOfInterest([0, 1], [1, 0])
+        kw = dict(omega=4, psi0=256, rhat=1.1, H_star=0.003, relative=False)
+    else:
+        # batch means of single values of a sticky chain (lag-1 correlation
+        # near 1 - 2p): the randomness test fails, the spacer steps up and the
+        # batch size grows by sqrt 2 several times before it passes
+        net, soi = S.identity_node(0.02), S.StateOfInterest([0], [1])
+        kw = dict(omega=8, psi0=256, rhat=1.1, H_star=0.02, relative=False)
     o = oracle.estimate_skart(net, soi, seed=5, alpha=0.05, **kw)
     assert o["status"] == 0
+    if case.endswith("multibatch"):
+        assert o["batches"] // kw["omega"] >= 80 and o["rand_rounds"] >= 1
+    if case == "identity-correlated":
+        assert o["rand_rounds"] > 10 and o["spacer"] > 0 and o["kappa"] > 16
     g = P.pbn_estimate_skart(P.pbn_load(net), soi, seed=5, alpha=0.05, **kw)
     for k in ("psi", "length", "kappa", "batches", "spacer", "sample_size", "gr_rounds", "rand_rounds", "ci_rounds"):
         assert g[k] == o[k], k
