@@ -480,6 +480,8 @@ typedef struct pbn_engine_stats {
     double sim_ms;                     /* CUDA-event time of this epoch's batch_sim_kernel launch (0: none) */
     int64_t sim_items;                 /* its (node, chain group, transition) items */
     int64_t d2h_bytes;                 /* device -> host bytes this epoch read (results, status) */
+    int32_t tuning;                    /* 1 while the autotuner is still timing candidates */
+    int32_t pad;
 } pbn_engine_stats;
 
 /* Create an engine on the current device.  It runs on a stream of its own,

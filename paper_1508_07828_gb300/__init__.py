@@ -152,7 +152,7 @@ class EngineStats(ctypes.Structure):
     _fields_ = [("epoch", c_i64), ("active", c_i32), ("pending", c_i32), ("finished", c_i64), ("updates", c_i64),
                 ("epoch_ms", c_dbl), ("hbm_in_use", c_i64), ("steps_per_epoch", c_i32),
                 ("threads_per_block", c_i32), ("items_per_thread", c_i32), ("kernel_launches", c_i32),
-                ("sim_ms", c_dbl), ("sim_items", c_i64), ("d2h_bytes", c_i64)]
+                ("sim_ms", c_dbl), ("sim_items", c_i64), ("d2h_bytes", c_i64), ("tuning", c_i32), ("pad", c_i32)]
 
 
 METHOD_TWO_STATE = 0

@@ -1017,6 +1017,7 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
     st->sim_ms = sim_ms;
     st->sim_items = sim_items;
     st->d2h_bytes = d2h;
+    st->tuning = e->best < 0 ? 1 : 0;
   }
   return PBN_OK;
 }

@@ -89,7 +89,7 @@ STRUCTS = {
                                            "admit_epoch", "finish_epoch"]),
     "EngineStats": ("pbn_engine_stats", ["epoch", "active", "pending", "finished", "updates", "epoch_ms",
                                          "hbm_in_use", "steps_per_epoch", "threads_per_block", "items_per_thread",
-                                         "kernel_launches", "sim_ms", "sim_items", "d2h_bytes"]),
+                                         "kernel_launches", "sim_ms", "sim_items", "d2h_bytes", "tuning"]),
 }
 
 
