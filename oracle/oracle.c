@@ -26,7 +26,7 @@
  *     values in (P32, T_0, .., T_{l-2}) that are <= u: category 0 means the
  *     node is perturbed (gamma_i = 1), category j+1 selects function j.
  *   - Truth table: value = bit j = (sum_m s[parent_m] << m) of the function's
- *     table, stored as words: bit j % 32 of word j / 32 (k <= 12 parents).
+ *     table, stored as words: bit j % 32 of word j / 32 (k <= 16 parents).
  *   - Perturbation reading PER_NODE (mode 0): a perturbed node flips, every
  *     other node takes its selected function's value.  Reading GLOBAL (mode 1):
  *     if any node is perturbed the next state is s XOR gamma, else every node
@@ -43,7 +43,7 @@
 #define ORC_ERR_INVALID 1
 #define ORC_ERR_OOM 2
 #define ORC_ERR_NOT_CONVERGED 5
-#define ORC_MAX_PARENTS 12
+#define ORC_MAX_PARENTS 16
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10, from the round function and key schedule published in       */

@@ -136,10 +136,15 @@ int plan_launch(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, in
     gpb = std::max(1, gpb / 2);
   }
   int T = T_req;
-  if (T == 0) T = (G < sm_count() && net.n * gpb * 2 <= 512 && !net.has_wide) ? 2 : 1;
+  const bool many = net.max_l > pbn::kMaxL || net.max_k > pbn::kWideK;
+  if (T == 0) T = (G < sm_count() && net.n * gpb * 2 <= 512 && !net.has_wide && !many) ? 2 : 1;
   if (T != 1 && T != 2 && T != 4) return fail(PBN_ERR_INVALID, "threads_per_item %d (1, 2 or 4)", T);
   if (net.has_wide && (T != 1 || (BPR_req && BPR_req != 1)))
     return fail(PBN_ERR_UNSUPPORTED, "functions with more than 5 inputs run one thread per item, one block per round");
+  if (many && (T != 1 || (BPR_req && BPR_req != 1)))
+    return fail(PBN_ERR_UNSUPPORTED,
+                "nodes with more than %d functions or functions of more than %d inputs run one thread per item, "
+                "one block per round", pbn::kMaxL, pbn::kWideK);
   int BPR = BPR_req ? BPR_req : 1;
   if (T == 2) BPR = 2;
   if (T == 4) BPR = 1;
@@ -184,6 +189,7 @@ pbn::SimArgs make_args(const pbn::NetDev &net, const pbn_run_cfg &cfg, const pbn
   a.wide_tt = net.d_wide_tt;
   a.wide_par = net.d_wide_par;
   a.has_wide = net.has_wide;
+  a.many = (net.max_l > pbn::kMaxL || net.max_k > pbn::kWideK) ? 1 : 0;
   a.status = status ? status : pbn::device_status();
   {
     static const int stall = getenv("PBN_TEST_STALL_FIRST_TILE") ? atoi(getenv("PBN_TEST_STALL_FIRST_TILE")) : 0;
@@ -294,6 +300,9 @@ int plan_select(const pbn::NetDev &net, int64_t omega, int mode, int gpb_req, in
   const int G = (int)((omega + 31) / 32);
   const int maxs = pbn::sim_max_smem();
   if (staging_req == 2) return fail(PBN_ERR_UNSUPPORTED, "select-ahead schedule with TMA tiles");
+  if (net.max_l > pbn::kMaxL || net.max_k > pbn::kWideK)
+    return fail(PBN_ERR_UNSUPPORTED, "select-ahead schedule with nodes of more than %d functions or functions of "
+                "more than %d inputs", pbn::kMaxL, pbn::kWideK);
   int gpb = gpb_req > 0 ? gpb_req : std::max(1, (G + sm_count() - 1) / sm_count());
   gpb = std::min(gpb, std::max(G, 1));
   const int W = (net.F + (mode == PBN_PERTURB_GLOBAL ? 1 : 0) + 3) & ~3;
@@ -702,7 +711,7 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
   // tables of functions with more than 5 inputs, and their parents
   std::vector<uint32_t> wide_tt;
   std::vector<uint16_t> wide_par;
-  int max_l = 0;
+  int max_l = 0, max_k = 0;
   for (int i = 0; i < n; i++) {
     const int f0 = d->fn_offset[i], f1 = d->fn_offset[i + 1];
     const int l = f1 - f0;
@@ -710,6 +719,7 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
     if (l > PBN_MAX_FUNCTIONS_PER_NODE)
       return fail(PBN_ERR_UNSUPPORTED, "node %d has %d functions (max %d)", i, l, PBN_MAX_FUNCTIONS_PER_NODE);
     max_l = std::max(max_l, l);
+    for (int f = f0; f < f1; f++) max_k = std::max(max_k, d->par_offset[f + 1] - d->par_offset[f]);
     double sum = 0.0, S = 0.0;
     uint64_t shape = (uint64_t)l;
     for (int f = f0; f < f1; f++) {
@@ -804,6 +814,7 @@ int pbn_load(const pbn_network_desc *d, pbn_net **out) {
   net->dev.F = F;
   net->dev.P32 = P32;
   net->dev.max_l = max_l;
+  net->dev.max_k = max_k;
   net->dev.ntiles = (int)tiles.size() - 1;
   net->dev.tile_bytes = max_tile * 16;
   // every table in one device allocation, filled by one copy: function

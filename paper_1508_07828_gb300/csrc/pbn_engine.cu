@@ -763,6 +763,9 @@ extern "C" int pbn_engine_submit(pbn_engine *e, const pbn_engine_query *qin, int
     q->soi_nodes.push_back(soi->nodes[m]);
     q->soi_vals.push_back(soi->values[m]);
   }
+  if (qin->net->dev.max_l > kMaxL || qin->net->dev.max_k > kWideK)
+    return efail(PBN_ERR_UNSUPPORTED,
+                 "the engine's batched kernel takes nodes of at most %d functions of at most %d inputs", kMaxL, kWideK);
   q->G = (int)((q->omega + 31) / 32);
   if ((int64_t)q->G * 1 > (1ll << 30)) return efail(PBN_ERR_UNSUPPORTED, "omega too large");
   q->id = e->next_id++;

@@ -8,7 +8,15 @@
 
 namespace pbn {
 
-constexpr int kMaxL = PBN_MAX_FUNCTIONS_PER_NODE;  // functions per node (thresholds per node incl. P32)
+// Functions per node (= category bounds per node, P32 included): the draw keeps
+// up to kMaxL bounds in registers; nodes with kMaxL+1 .. kMaxLAll functions
+// (the dense class of the paper's sweep) take an out-of-line variant.
+constexpr int kMaxL = 8;
+constexpr int kMaxLAll = PBN_MAX_FUNCTIONS_PER_NODE;
+// Inputs of one function: the common kernels gather up to kWideK parents per
+// looked-up chain; networks with more (up to PBN_MAX_PARENTS) take the same
+// out-of-line variant as those with more than kMaxL functions per node.
+constexpr int kWideK = 12;
 constexpr int kMaxSoi = PBN_MAX_SOI;
 constexpr int kMaxProps = PBN_MAX_PROPERTIES;
 
@@ -19,12 +27,13 @@ constexpr int kMaxProps = PBN_MAX_PROPERTIES;
 //    y = upper category bound T_j (unused for the last function of a node)
 //    z = p0 | p1 << 12 | (p4 & 0xFF) << 24
 //    w = p2 | p3 << 12 | (p4 >> 8) << 24 | k << 28
-//  k = 6 .. 12 inputs ("wide"): x = first of its 2^(k-5) table words in
+//  k = 6 .. 16 inputs ("wide"): x = first of its 2^(k-5) table words in
 //    d_wide_tt, z = first of its k parents in d_wide_par, w = k << 28
 struct NetDev {
   int n = 0, F = 0;
   uint32_t P32 = 0;
   int max_l = 0;
+  int max_k = 0;                  // most inputs of one function
   uint32_t *d_node = nullptr;
   uint4 *d_fn = nullptr;          // function records in processing order
   int32_t *d_tiles = nullptr;     // [ntiles+1] first processing position of each tile
@@ -110,6 +119,8 @@ struct SimArgs {
   const uint32_t *wide_tt;   // tables and parents of functions with more than 5 inputs (NetDev)
   const uint16_t *wide_par;
   int has_wide;
+  int many;              // some node has more than kMaxL functions or some function more than kWideK
+                         // inputs (the fused kernel's kMaxLAll / PBN_MAX_PARENTS variant)
   int W;                 // select-ahead: category words per (step, group): F (+1 under global
                          // perturbation: word F is the OR of the perturbed lanes), rounded up to 4
   uint32_t *planes;      // select-ahead: category words [steps][G][W] of the chunk

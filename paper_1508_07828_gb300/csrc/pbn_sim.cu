@@ -37,8 +37,9 @@
 namespace pbn {
 
 // WIDE: the variant for networks with functions of more than 5 inputs (one
-// thread per item, one Philox block per round only).
-template <int MODE, int T, int BPR, bool WIDE>
+// thread per item, one Philox block per round only).  LMAX: functions per node
+// (kMaxLAll in the variant for networks with nodes of more than kMaxL).
+template <int MODE, int T, int BPR, bool WIDE, int LMAX = kMaxL>
 __global__ void __launch_bounds__(max_threads<T>()) sim_kernel(const __grid_constant__ SimArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   int g0 = (int)blockIdx.x * a.gpb, ngl = min(a.gpb, a.G - g0), nsteps = a.steps, soff = 0;
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(max_threads<T>()) sim_kernel(const __grid_cons
     soff = a.seg_soff[q];
   }
   // layout stride ngl: a CTA with fewer groups than a.gpb runs fewer item rounds
-  cta_simulate<MODE, T, BPR, WIDE>(a, a.rk, (uint32_t)g0, ngl, ngl, smem, nsteps, soff);
+  cta_simulate<MODE, T, BPR, WIDE, LMAX>(a, a.rk, (uint32_t)g0, ngl, ngl, smem, nsteps, soff);
 }
 
 __global__ void init_kernel(const __grid_constant__ RoundKeys rk, uint32_t *state, int n, int G, int64_t omega) {
@@ -106,22 +107,26 @@ int sim_max_smem() {
   return v;
 }
 
-template <int MODE, int T, int BPR, bool WIDE = false>
+template <int MODE, int T, int BPR, bool WIDE = false, int LMAX = kMaxL>
 static cudaError_t launch_variant(const SimArgs &a, int blocks, int threads, size_t smem, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(sim_kernel<MODE, T, BPR, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         sim_max_smem());
+    cudaError_t e = cudaFuncSetAttribute(sim_kernel<MODE, T, BPR, WIDE, LMAX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sim_max_smem());
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  sim_kernel<MODE, T, BPR, WIDE><<<blocks, threads, smem, s>>>(a);
+  sim_kernel<MODE, T, BPR, WIDE, LMAX><<<blocks, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int MODE>
 static cudaError_t launch_mode(const SimArgs &a, int T, int BPR, int blocks, int threads, size_t smem,
                                cudaStream_t s) {
+  if (a.many) {
+    if (T != 1 || BPR != 1) return cudaErrorInvalidValue;  // the planner gives such networks T = 1, BPR = 1
+    return launch_variant<MODE, 1, 1, true, kMaxLAll>(a, blocks, threads, smem, s);
+  }
   if (a.has_wide) {
     if (T != 1 || BPR != 1) return cudaErrorInvalidValue;  // the planner gives wide networks T = 1, BPR = 1
     return launch_variant<MODE, 1, 1, true>(a, blocks, threads, smem, s);

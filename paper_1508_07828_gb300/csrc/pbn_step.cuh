@@ -74,19 +74,22 @@ __device__ __forceinline__ uint32_t eval_uniform(int K, uint4 rec, int k, const 
 // index gathers bit q of the k parents' state words, and bit q of the result
 // is that entry of the table.  Over an item's functions every chain is looked
 // up once.
+// KMAX: most inputs the variant takes (kWideK, or PBN_MAX_PARENTS in the
+// kernels for the sweep's dense class).
+template <int KMAX = kWideK>
 static __device__ __noinline__ uint32_t eval_wide_lanes(uint4 rec, uint32_t lanes, const uint32_t *cur, int gpb,
                                                         int gl, const uint32_t *wide_tt, const uint16_t *wide_par) {
   const int k = fn_k(rec);
-  uint32_t w[PBN_MAX_PARENTS];
+  uint32_t w[KMAX];
 #pragma unroll
-  for (int m = 0; m < PBN_MAX_PARENTS; m++) w[m] = m < k ? cur[(int)wide_par[rec.z + m] * gpb + gl] : 0u;
+  for (int m = 0; m < KMAX; m++) w[m] = m < k ? cur[(int)wide_par[rec.z + m] * gpb + gl] : 0u;
   uint32_t out = 0u;
   while (lanes) {
     const int q = __ffs(lanes) - 1;
     lanes &= lanes - 1;
     uint32_t idx = 0u;
 #pragma unroll
-    for (int m = 0; m < PBN_MAX_PARENTS; m++) idx |= ((w[m] >> q) & 1u) << m;
+    for (int m = 0; m < KMAX; m++) idx |= ((w[m] >> q) & 1u) << m;
     out |= ((wide_tt[rec.x + (idx >> 5)] >> (idx & 31u)) & 1u) << q;
   }
   return out;
@@ -216,7 +219,9 @@ __device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, con
       const int kt = wide ? 0 : k;
       const int K = __reduce_max_sync(kFull, (unsigned)kt);
       if (__any_sync(kFull, has && !wide)) fword |= (wide ? 0u : my_sel) & eval_uniform(K, tr, kt, c.cur, c.gpb, c.gl);
-      if (wide) fword |= eval_wide_lanes(rec, my_sel, c.cur, c.gpb, c.gl, c.wide_tt, c.wide_par);
+      if (wide)
+        fword |= eval_wide_lanes<(LW > kMaxL ? PBN_MAX_PARENTS : kWideK)>(rec, my_sel, c.cur, c.gpb, c.gl, c.wide_tt,
+                                                                          c.wide_par);
     } else {
       const int K = __reduce_max_sync(kFull, (unsigned)k);
       if (__any_sync(kFull, has)) fword |= my_sel & eval_uniform(K, rec, k, c.cur, c.gpb, c.gl);
@@ -242,13 +247,16 @@ __device__ __forceinline__ uint32_t lane_mask(int64_t omega, uint32_t g) {
 }
 
 // Nodes with more than 4 functions are rare; their variant is kept out of
-// line so its register demand does not raise the common path's.
-template <int MODE, int T, int BPR, bool WIDE>
+// line so its register demand does not raise the common path's.  LMAX bounds
+// the functions per node: kMaxL in the common kernels, kMaxLAll in the
+// variant for networks of the sweep's dense class (a separate kernel, so the
+// common kernels' register allocation does not see the wider arrays).
+template <int MODE, int T, int BPR, bool WIDE, int LMAX>
 __device__ __noinline__ void step_item_wide(const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
-  step_item<kMaxL, MODE, T, BPR, WIDE>(rk, P32, c);
+  step_item<LMAX, MODE, T, BPR, WIDE>(rk, P32, c);
 }
 
-template <int MODE, int T, int BPR, bool WIDE>
+template <int MODE, int T, int BPR, bool WIDE, int LMAX>
 __device__ __forceinline__ void dispatch_item(int LW, const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
   switch (LW) {
     case 0: break;
@@ -256,7 +264,7 @@ __device__ __forceinline__ void dispatch_item(int LW, const RoundKeys &rk, uint3
     case 2: step_item<2, MODE, T, BPR, WIDE>(rk, P32, c); break;
     case 3: step_item<3, MODE, T, BPR, WIDE>(rk, P32, c); break;
     case 4: step_item<4, MODE, T, BPR, WIDE>(rk, P32, c); break;
-    default: step_item_wide<MODE, T, BPR, WIDE>(rk, P32, c); break;
+    default: step_item_wide<MODE, T, BPR, WIDE, LMAX>(rk, P32, c); break;
   }
 }
 
@@ -317,7 +325,7 @@ constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: a 24 KB tile arrives i
 // Function records come from shared memory (whole tables), from TMA tiles
 // streamed through two shared buffers (tile u of the launch's sequence
 // s*ntiles + t goes to buffer u & 1), or straight from global memory.
-template <int MODE, int T, int BPR, bool WIDE>
+template <int MODE, int T, int BPR, bool WIDE, int LMAX = kMaxL>
 __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &rk, uint32_t g0, int ngl, int gpb,
                                              unsigned char *smem, int nsteps, int64_t soff) {
   if (ngl <= 0) return;  // CTA-uniform
@@ -437,7 +445,7 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
         c.g = g0 + (uint32_t)c.gl;
         c.vmask = c.active ? lane_mask(a.omega, c.g) : 0u;
         const int LW = (int)__reduce_max_sync(kFull, (unsigned)c.L);
-        dispatch_item<MODE, T, BPR, WIDE>(LW, rk, P32, c);
+        dispatch_item<MODE, T, BPR, WIDE, LMAX>(LW, rk, P32, c);
       }
       __syncthreads();
       if (staging == STAGE_TILES && threadIdx.x == 0) {

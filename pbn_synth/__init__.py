@@ -18,7 +18,7 @@ Network format (the PBN G(V, F) of Sec. 2.2, in CSR form):
 * ``tt_offset``    int32[F+1]; function f's truth table is the words
                    ``tt_words[tt_offset[f] : tt_offset[f+1]]``, max(1, 2^k / 32)
                    of them; the value of f on parent values (x_0..x_{k-1}) is
-                   bit j % 32 of word j / 32, j = sum_m x_m 2^m (k <= 12)
+                   bit j % 32 of word j / 32, j = sum_m x_m 2^m (k <= 16)
 * ``tt_words``     uint32[...]
 * ``truth_table``  uint32[F]; each function's first word (its whole table
                    when k <= 5)
@@ -212,10 +212,10 @@ def wide_config(seed: int = BASE_SEED + 5, n: int = 4096) -> tuple:
 
 # Density classes of the paper's sweep (Sec. 5.1): the density D(G) is the
 # parent count of all functions over n, about (functions per node) x (parents
-# per function).  Sparse ~10 and in-between 50-100 are drawn here; dense
-# (150-300) needs more functions or inputs than this build takes (8 functions
-# of at most 12 inputs give at most 96).
-DENSITY_CLASSES = {"sparse": ((2, 4), (2, 5)), "in-between": ((6, 8), (7, 12))}
+# per function).  Sparse ~10: 2-4 functions of 2-5 parents; in-between 50-100:
+# 6-8 functions of 7-12 parents; dense 150-300: 12-16 functions of 10-16
+# parents (D about 14 x 13 = 182; truth tables of 32-2048 words).
+DENSITY_CLASSES = {"sparse": ((2, 4), (2, 5)), "in-between": ((6, 8), (7, 12)), "dense": ((12, 16), (10, 16))}
 
 
 def sweep_config(n: int, density: str, seed: int = BASE_SEED + 7) -> tuple:
@@ -223,7 +223,7 @@ def sweep_config(n: int, density: str, seed: int = BASE_SEED + 7) -> tuple:
     function and parent ranges, biased truth tables, p = 0.001; state of
     interest: 3 random nodes with random values."""
     fns, pars = DENSITY_CLASSES[density]
-    s = seed + 1000 * n + (0 if density == "sparse" else 1)
+    s = seed + 1000 * n + {"sparse": 0, "in-between": 1, "dense": 2}[density]
     net = random_pbn(s, n, fns, pars, "biased", "uniform", 0.001, f"sweep-{density}-n{n}")
     soi = random_soi(np.random.default_rng(s), n, 3, 3)
     return net, soi
