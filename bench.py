@@ -86,7 +86,7 @@ def parse():
     ap.add_argument("--sweep", action="store_true", help="the paper's n x density sweep at precision --seq-r")
     ap.add_argument("--sweep-omega", type=int, default=2048)
     ap.add_argument("--sweep-seq-max-n", type=int, default=100)
-    ap.add_argument("--sweep-classes", default="sparse,in-between", help="density classes of --sweep")
+    ap.add_argument("--sweep-classes", default="sparse,in-between,dense", help="density classes of --sweep")
     ap.add_argument("--sweep-seq-classes", default="sparse",
                     help="classes whose smallest models also run the sequential Alg. 1 (minutes per model otherwise)")
     ap.add_argument("--multi", type=int, default=0,

@@ -64,7 +64,10 @@ constexpr int kCounters = 8;     // items, next item, virtual blocks, next virtu
 
 // ------------------------------------------------------------------ kernels
 
-__global__ void __launch_bounds__(512) batch_sim_kernel(const SimArgs *__restrict__ tasks,
+// At most 80 registers (a few bytes spill), so that three 256-thread CTAs
+// share an SM: 24 warps to hide the dependent Philox rounds, against 16 when
+// the compiler takes 108.
+__global__ void __maxnreg__(80) batch_sim_kernel(const SimArgs *__restrict__ tasks,
                                                         const BatchItem *__restrict__ items, int *counters) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) SimArgs s_task;
@@ -330,6 +333,24 @@ int smem_limit() {
     v = sim_max_smem() - (int)stat;
   }
   return v;
+}
+
+// Dynamic shared memory per CTA for a CTA size: 256-thread CTAs are sized so
+// that three share an SM (the kernel is held to 80 registers, which three
+// 256-thread CTAs fit), 512-thread CTAs take one SM each.
+int smem_cap_for(int threads) {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) per_sm = 0;
+  }
+  if (threads > 256 || per_sm <= 0) return smem_limit();
+  cudaFuncAttributes fa;
+  size_t stat = 0;
+  if (cudaFuncGetAttributes(&fa, batch_sim_kernel) == cudaSuccess) stat = fa.sharedSizeBytes;
+  // each CTA also takes 1 KB of shared memory that the system reserves
+  return std::min(smem_limit(), per_sm / 3 - 1024 - (int)stat);
 }
 
 // Chain groups per CTA for one query: about threads * ipt items, at most
@@ -783,7 +804,7 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
   int ci = e->best;
   if (ci < 0) ci = e->round_robin++ % (int)e->cands.size();
   const Candidate &cand = e->cands[ci];
-  size_t smem_cap = (size_t)smem_limit();
+  size_t smem_cap = (size_t)smem_cap_for(cand.threads);
   e->epoch_queries.clear();
   // spread light epochs: at least about two CTAs per SM when the active
   // chain groups allow it
