@@ -170,8 +170,11 @@ def test_probabilities_are_checked(P):
 def test_limits_are_checked(P):
     big = S.random_pbn(1, 4097, (1, 1), (1, 1), "fair", "uniform", 0.01)  # PBN_MAX_NODES + 1
     assert _status(P, big) == P.PBN_ERR_UNSUPPORTED
-    nine = S.from_lists(1, [[((0,), 0b10, 1 / 9)] * 9], 0.01)  # nine functions on one node
-    assert _status(P, nine) == P.PBN_ERR_UNSUPPORTED
+    many = S.from_lists(1, [[((0,), 0b10, 1 / 17)] * 17], 0.01)  # PBN_MAX_FUNCTIONS_PER_NODE + 1 functions
+    assert _status(P, many) == P.PBN_ERR_UNSUPPORTED
+    # PBN_MAX_PARENTS + 1 inputs
+    wide = S.random_pbn(3, 18, (1, 1), (17, 17), "fair", "uniform", 0.01)
+    assert _status(P, wide) == P.PBN_ERR_UNSUPPORTED
     # a 6-input function without a multi-word table
     six = _net(par_offset=np.array([0, 6, 7, 8, 10], np.int32),
                parents=np.array([1, 2, 0, 1, 2, 0, 0, 2, 0, 1], np.int32))
