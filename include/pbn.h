@@ -58,7 +58,7 @@ enum { PBN_PERTURB_PER_NODE = 0, PBN_PERTURB_GLOBAL = 1 };
 
 /* Limits of this build. */
 #define PBN_MAX_NODES 4096          /* node ids are 12-bit in the device tables */
-#define PBN_MAX_PARENTS 16          /* truth tables up to 65536 bits (2048 words) */
+#define PBN_MAX_PARENTS 15          /* truth tables up to 32768 bits (1024 words) */
 #define PBN_MAX_FUNCTIONS_PER_NODE 16
 #define PBN_MAX_SOI 32               /* state-of-interest entries of one run, over all its properties */
 #define PBN_MAX_PROPERTIES 8         /* properties abstracted from one set of trajectories (Sec. 4.2) */

@@ -17,6 +17,7 @@ constexpr int kMaxLAll = PBN_MAX_FUNCTIONS_PER_NODE;
 // looked-up chain; networks with more (up to PBN_MAX_PARENTS) take the same
 // out-of-line variant as those with more than kMaxL functions per node.
 constexpr int kWideK = 12;
+static_assert(PBN_MAX_PARENTS <= 15, "a function record keeps its input count in 4 bits");
 constexpr int kMaxSoi = PBN_MAX_SOI;
 constexpr int kMaxProps = PBN_MAX_PROPERTIES;
 
@@ -27,7 +28,7 @@ constexpr int kMaxProps = PBN_MAX_PROPERTIES;
 //    y = upper category bound T_j (unused for the last function of a node)
 //    z = p0 | p1 << 12 | (p4 & 0xFF) << 24
 //    w = p2 | p3 << 12 | (p4 >> 8) << 24 | k << 28
-//  k = 6 .. 16 inputs ("wide"): x = first of its 2^(k-5) table words in
+//  k = 6 .. 15 inputs ("wide"): x = first of its 2^(k-5) table words in
 //    d_wide_tt, z = first of its k parents in d_wide_par, w = k << 28
 struct NetDev {
   int n = 0, F = 0;

@@ -18,7 +18,7 @@ Network format (the PBN G(V, F) of Sec. 2.2, in CSR form):
 * ``tt_offset``    int32[F+1]; function f's truth table is the words
                    ``tt_words[tt_offset[f] : tt_offset[f+1]]``, max(1, 2^k / 32)
                    of them; the value of f on parent values (x_0..x_{k-1}) is
-                   bit j % 32 of word j / 32, j = sum_m x_m 2^m (k <= 16)
+                   bit j % 32 of word j / 32, j = sum_m x_m 2^m (k <= 15)
 * ``tt_words``     uint32[...]
 * ``truth_table``  uint32[F]; each function's first word (its whole table
                    when k <= 5)
@@ -213,9 +213,9 @@ def wide_config(seed: int = BASE_SEED + 5, n: int = 4096) -> tuple:
 # Density classes of the paper's sweep (Sec. 5.1): the density D(G) is the
 # parent count of all functions over n, about (functions per node) x (parents
 # per function).  Sparse ~10: 2-4 functions of 2-5 parents; in-between 50-100:
-# 6-8 functions of 7-12 parents; dense 150-300: 12-16 functions of 10-16
-# parents (D about 14 x 13 = 182; truth tables of 32-2048 words).
-DENSITY_CLASSES = {"sparse": ((2, 4), (2, 5)), "in-between": ((6, 8), (7, 12)), "dense": ((12, 16), (10, 16))}
+# 6-8 functions of 7-12 parents; dense 150-300: 12-16 functions of 10-15
+# parents (D about 14 x 12.5 = 175; truth tables of 32-1024 words).
+DENSITY_CLASSES = {"sparse": ((2, 4), (2, 5)), "in-between": ((6, 8), (7, 12)), "dense": ((12, 16), (10, 15))}
 
 
 def sweep_config(n: int, density: str, seed: int = BASE_SEED + 7) -> tuple:

@@ -1,5 +1,5 @@
 """The dense class of the paper's sweep (Sec. 5.1, density 150-300: 12-16
-functions of 10-16 inputs per node) on the CUDA path: trajectories and
+functions of 10-15 inputs per node) on the CUDA path: trajectories and
 indicator bitstreams bit-exact against the oracle under both perturbation
 readings (the fused kernel's variant for nodes with more than 8 functions),
 whole queries equal to the oracle's, sampled chains of a sweep-sized model,
@@ -23,14 +23,14 @@ def P():
 
 
 def _dense(n=16, seed=1616):
-    return S.random_pbn(seed, n, (12, 16), (10, min(16, n)), "biased", "uniform", 0.05, f"dense-n{n}")
+    return S.random_pbn(seed, n, (12, 16), (10, min(15, n)), "biased", "uniform", 0.05, f"dense-n{n}")
 
 
 NETS = [
     ("dense-n16", _dense(), S.StateOfInterest([0, 7], [1, 0]), 70),
     ("dense-n14-k14", _dense(14, 1414), S.StateOfInterest([0, 3], [1, 0]), 33),
     ("sweep-dense-n80", *S.sweep_config(80, "dense"), 40),
-    ("mixed-l", S.random_pbn(99, 24, (1, 16), (2, 16), "fair", "uniform", 0.02), S.StateOfInterest([2], [1]), 64),
+    ("mixed-l", S.random_pbn(99, 24, (1, 16), (2, 15), "fair", "uniform", 0.02), S.StateOfInterest([2], [1]), 64),
 ]
 
 

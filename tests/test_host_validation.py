@@ -173,7 +173,7 @@ def test_limits_are_checked(P):
     many = S.from_lists(1, [[((0,), 0b10, 1 / 17)] * 17], 0.01)  # PBN_MAX_FUNCTIONS_PER_NODE + 1 functions
     assert _status(P, many) == P.PBN_ERR_UNSUPPORTED
     # PBN_MAX_PARENTS + 1 inputs
-    wide = S.random_pbn(3, 18, (1, 1), (17, 17), "fair", "uniform", 0.01)
+    wide = S.random_pbn(3, 18, (1, 1), (16, 16), "fair", "uniform", 0.01)
     assert _status(P, wide) == P.PBN_ERR_UNSUPPORTED
     # a 6-input function without a multi-word table
     six = _net(par_offset=np.array([0, 6, 7, 8, 10], np.int32),

@@ -1,6 +1,6 @@
 """Pins of the oracle on the dense class of the paper's sweep (Sec. 5.1:
-density D(G) 150-300, here 12-16 predictor functions of 10-16 parents per
-node, truth tables of 32-2048 words): the recipe's density, the one-step
+density D(G) 150-300, here 12-16 predictor functions of 10-15 parents per
+node, truth tables of 32-1024 words): the recipe's density, the one-step
 law from given states (every node's next value and the joint law of four
 nodes, against probabilities computed here from the truth tables and the
 quantised selection probabilities), and the whole method within r of the
@@ -14,7 +14,7 @@ from oracle import exact
 
 
 def _dense(n=16, seed=1616):
-    return S.random_pbn(seed, n, (12, 16), (10, min(16, n)), "biased", "uniform", 0.05, f"dense-n{n}")
+    return S.random_pbn(seed, n, (12, 16), (10, min(15, n)), "biased", "uniform", 0.05, f"dense-n{n}")
 
 
 def test_recipe_density_in_the_dense_class():
@@ -22,7 +22,7 @@ def test_recipe_density_in_the_dense_class():
         net, soi = S.sweep_config(n, "dense")
         assert 150 <= net.density() <= 300, (n, net.density())
         ks = np.diff(net.par_offset)
-        assert ks.min() >= 10 and ks.max() == 16
+        assert ks.min() >= 10 and ks.max() == 15
         assert np.diff(net.fn_offset).max() == 16 and np.diff(net.fn_offset).min() == 12
     net = _dense()
     assert 150 <= net.density() <= 300
