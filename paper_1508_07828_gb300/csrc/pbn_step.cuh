@@ -203,7 +203,7 @@ __device__ __forceinline__ void select_masks(const uint32_t (&lt)[LW], uint32_t 
 // One item of one transition: category draw, then the selected functions.
 // WIDE: compiled with the lookup of functions with more than 5 inputs (used
 // when c.has_wide); without it the code is the common path alone.
-template <int LW, int MODE, int T, int BPR, bool WIDE>
+template <int LW, int MODE, int T, int BPR, bool WIDE, int KMAX = kWideK>
 __device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
   uint32_t lt[LW];
   draw_below<LW, T, BPR>(rk, P32, c, lt);
@@ -226,9 +226,7 @@ __device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, con
       const int kt = wide ? 0 : k;
       const int K = __reduce_max_sync(kFull, (unsigned)kt);
       if (__any_sync(kFull, has && !wide)) fword |= (wide ? 0u : my_sel) & eval_uniform(K, tr, kt, c.cur, c.gpb, c.gl);
-      if (wide)
-        fword |= eval_wide_lanes<(LW > kMaxL ? PBN_MAX_PARENTS : kWideK)>(rec, my_sel, c.cur, c.gpb, c.gl, c.wide_tt,
-                                                                          c.wide_par);
+      if (wide) fword |= eval_wide_lanes<KMAX>(rec, my_sel, c.cur, c.gpb, c.gl, c.wide_tt, c.wide_par);
     } else {
       const int K = __reduce_max_sync(kFull, (unsigned)k);
       if (__any_sync(kFull, has)) fword |= my_sel & eval_uniform(K, rec, k, c.cur, c.gpb, c.gl);
@@ -258,19 +256,25 @@ __device__ __forceinline__ uint32_t lane_mask(int64_t omega, uint32_t g) {
 // the functions per node: kMaxL in the common kernels, kMaxLAll in the
 // variant for networks of the sweep's dense class (a separate kernel, so the
 // common kernels' register allocation does not see the wider arrays).
+// The variant with more functions per node also takes functions of up to
+// PBN_MAX_PARENTS inputs (the common kernels: kWideK).
+template <int LMAX>
+__host__ __device__ constexpr int kmax_of() { return LMAX > kMaxL ? PBN_MAX_PARENTS : kWideK; }
+
 template <int MODE, int T, int BPR, bool WIDE, int LMAX>
 __device__ __noinline__ void step_item_wide(const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
-  step_item<LMAX, MODE, T, BPR, WIDE>(rk, P32, c);
+  step_item<LMAX, MODE, T, BPR, WIDE, kmax_of<LMAX>()>(rk, P32, c);
 }
 
 template <int MODE, int T, int BPR, bool WIDE, int LMAX>
 __device__ __forceinline__ void dispatch_item(int LW, const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
+  constexpr int K = kmax_of<LMAX>();
   switch (LW) {
     case 0: break;
-    case 1: step_item<1, MODE, T, BPR, WIDE>(rk, P32, c); break;
-    case 2: step_item<2, MODE, T, BPR, WIDE>(rk, P32, c); break;
-    case 3: step_item<3, MODE, T, BPR, WIDE>(rk, P32, c); break;
-    case 4: step_item<4, MODE, T, BPR, WIDE>(rk, P32, c); break;
+    case 1: step_item<1, MODE, T, BPR, WIDE, K>(rk, P32, c); break;
+    case 2: step_item<2, MODE, T, BPR, WIDE, K>(rk, P32, c); break;
+    case 3: step_item<3, MODE, T, BPR, WIDE, K>(rk, P32, c); break;
+    case 4: step_item<4, MODE, T, BPR, WIDE, K>(rk, P32, c); break;
     default: step_item_wide<MODE, T, BPR, WIDE, LMAX>(rk, P32, c); break;
   }
 }
