@@ -590,8 +590,11 @@ void retire(pbn_engine *e) {
 
 int capture_graph(pbn_engine *e, int threads, size_t smem) {
   if (e->exec && e->graph_threads == threads && e->graph_smem >= smem) return PBN_OK;
+  // the same CTA size keeps the largest shared-memory size seen (epochs of
+  // other mixes then reuse the graph); another CTA size starts afresh, since
+  // its CTAs per SM depend on it
+  const size_t gsmem = e->exec && e->graph_threads == threads ? std::max(smem, e->graph_smem) : smem;
   if (e->exec) { cudaGraphExecDestroy(e->exec); e->exec = nullptr; }
-  size_t gsmem = std::max(smem, e->graph_smem);
   int per_sm = 0;
   ECUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sim_kernel, threads, gsmem), "occupancy");
   const int sim_blocks = std::max(1, per_sm) * e->sms;
@@ -695,8 +698,10 @@ extern "C" int pbn_engine_create(const pbn_engine_cfg *cfg, void *stream, pbn_en
   memset(e->h_cnt, 0, sizeof(int) * kCounters);
   ECUDA(cudaFuncSetAttribute(batch_sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit()), "smem attr");
   // candidates of the autotuner (a fixed setting leaves one candidate)
+  // 512-thread CTAs (one per SM at 80 registers) measured slower than three
+  // 256-thread CTAs per SM on every setting tried, so the tuner keeps 256
   const int Ss[] = {1024, 4096};
-  const int Ts[] = {256, 512};
+  const int Ts[] = {256};
   const int Is[] = {2, 8};
   const int Bs[] = {STAGE_TILES, STAGE_GLOBAL};
   for (int S : Ss)

@@ -148,13 +148,6 @@ __device__ __forceinline__ void draw_below(const RoundKeys &rk, uint32_t P32, co
 #pragma unroll
       for (int m = 0; m < LW; m++) {
         const uint32_t tsb = ts[m] << (4u * b);
-        if (T == 1 && m == 0 && (tsb >> 28) == 0u) {
-          // bound 0 is P32, the same for every thread, and with one thread per
-          // item b is warp-uniform: when its four digits here are all 0, a
-          // lane with a 1 digit is above P32 and the rest stay tied
-          u[0] &= ~(Rq[0] | Rq[1] | Rq[2] | Rq[3]);
-          continue;
-        }
 #pragma unroll
         for (int q = 0; q < 4; q++) {
           // bound digit as 0 / ~0; lanes whose digit differs are decided
