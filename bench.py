@@ -93,6 +93,8 @@ def parse():
                     help="Q properties from the same trajectories against Q separate queries (mid workload)")
     ap.add_argument("--rates", default="50,200,1000,2000", help="arrival rates (queries/s) for --serve")
     ap.add_argument("--queries", type=int, default=1000, help="queries per rate for --serve")
+    ap.add_argument("--epoch-ms", type=float, default=6.0,
+                    help="--serve: the engine's latency bound per epoch (pbn_engine_cfg.epoch_target_ms)")
     ap.add_argument("--max-length", type=int, default=1 << 20)
     return ap.parse_args()
 
@@ -1127,8 +1129,8 @@ def run_serve(args):
             i = int(rng.integers(len(pool)))
             qs.append((i, S.random_soi(rng, pool[i].n), float(rng.choice([0.01, 0.005, 0.001])), 10_000 + k,
                        "ts" if rng.random() < 0.5 else "sk"))
-        # engine, continuous batching
-        eng = P.Engine(use_graph=True)
+        # engine, continuous batching, epochs bounded for latency
+        eng = P.Engine(use_graph=True, epoch_target_ms=args.epoch_ms)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         nxt, lat, upd, done, ok = 0, [], 0, 0, 0

@@ -448,6 +448,13 @@ typedef struct pbn_engine_cfg {
     int32_t threads_per_block;  /* 256 or 512; 0 = autotuned */
     int32_t items_per_thread;   /* (node, chain group) items per thread when sizing CTAs; 0 = autotuned */
     int32_t use_graph;          /* 1: each epoch is a captured CUDA graph, replayed */
+    /* Latency bound for serving: when > 0, a query's extension in one epoch is
+     * capped at about this many milliseconds of device time (estimated from the
+     * rates of earlier epochs, at least 64 transitions), so that queries that
+     * arrive wait at most about that long for the next epoch to admit them.
+     * 0: epochs end only at steps_per_epoch or a query's next check (more work
+     * per launch, the better setting for a batch submitted at once). */
+    double epoch_target_ms;
 } pbn_engine_cfg;
 
 typedef struct pbn_engine_query {

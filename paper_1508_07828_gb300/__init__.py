@@ -136,7 +136,8 @@ class SkartReport(ctypes.Structure):
 
 class EngineCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", c_i64), ("max_active", c_i32), ("steps_per_epoch", c_i32),
-                ("threads_per_block", c_i32), ("items_per_thread", c_i32), ("use_graph", c_i32)]
+                ("threads_per_block", c_i32), ("items_per_thread", c_i32), ("use_graph", c_i32),
+                ("epoch_target_ms", c_dbl)]
 
 
 class EngineQuery(ctypes.Structure):
@@ -563,9 +564,10 @@ class Engine:
     device-memory budget allow."""
 
     def __init__(self, hbm_budget_bytes: int = 0, max_active: int = 0, steps_per_epoch: int = 0,
-                 threads_per_block: int = 0, items_per_thread: int = 0, use_graph: bool = True, stream=None):
+                 threads_per_block: int = 0, items_per_thread: int = 0, use_graph: bool = True,
+                 epoch_target_ms: float = 0.0, stream=None):
         cfg = EngineCfg(int(hbm_budget_bytes), int(max_active), int(steps_per_epoch), int(threads_per_block),
-                        int(items_per_thread), int(bool(use_graph)))
+                        int(items_per_thread), int(bool(use_graph)), float(epoch_target_ms))
         h = c_vp()
         _check(lib().pbn_engine_create(ctypes.byref(cfg), _stream(stream), ctypes.byref(h)))
         self.handle = h

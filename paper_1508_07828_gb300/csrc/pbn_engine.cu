@@ -60,6 +60,9 @@ union ReqOut {
 };
 
 constexpr int kReqBlocks = 64;   // most virtual blocks of one statistics request
+// With a latency bound (pbn_engine_cfg.epoch_target_ms) an epoch's extension
+// of a query is never below kMinEpochSteps transitions.
+constexpr int64_t kMinEpochSteps = 64;
 constexpr int kCounters = 8;     // items, next item, virtual blocks, next virtual block, requests
 
 // ------------------------------------------------------------------ kernels
@@ -310,6 +313,8 @@ struct pbn_engine {
   std::vector<Candidate> cands;
   int best = -1;
   int round_robin = 0;
+  double items_per_ms = 0;   // batch_sim_kernel rate (moving average over epochs)
+  int sim_ctas = 0;          // CTAs of its last persistent grid
 };
 
 namespace {
@@ -598,6 +603,7 @@ int capture_graph(pbn_engine *e, int threads, size_t smem) {
   int per_sm = 0;
   ECUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sim_kernel, threads, gsmem), "occupancy");
   const int sim_blocks = std::max(1, per_sm) * e->sms;
+  e->sim_ctas = sim_blocks;
   cudaGraph_t g;
   ECUDA(cudaStreamBeginCapture(e->s, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaMemcpyAsync(e->d_tasks, e->h_tasks, sizeof(SimArgs) * e->cfg.max_active, cudaMemcpyHostToDevice, e->s);
@@ -623,6 +629,7 @@ int launch_direct(pbn_engine *e, int threads, size_t smem, int ntask, int nitems
   int per_sm = 0;
   ECUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sim_kernel, threads, smem), "occupancy");
   const int sim_blocks = std::max(1, std::min(std::max(1, per_sm) * e->sms, nitems));
+  e->sim_ctas = std::max(1, per_sm) * e->sms;
   if (ntask) ECUDA(cudaMemcpyAsync(e->d_tasks, e->h_tasks, sizeof(SimArgs) * ntask, cudaMemcpyHostToDevice, e->s), "tasks");
   if (nitems) ECUDA(cudaMemcpyAsync(e->d_items, e->h_items, sizeof(BatchItem) * nitems, cudaMemcpyHostToDevice, e->s), "items");
   if (nreq) ECUDA(cudaMemcpyAsync(e->d_reqs, e->h_reqs, sizeof(StatReq) * nreq, cudaMemcpyHostToDevice, e->s), "reqs");
@@ -653,6 +660,7 @@ extern "C" int pbn_engine_create(const pbn_engine_cfg *cfg, void *stream, pbn_en
   if (c.max_active <= 0) c.max_active = PBN_ENGINE_MAX_ACTIVE;
   if (c.max_active > PBN_ENGINE_MAX_ACTIVE) return efail(PBN_ERR_INVALID, "max_active above %d", PBN_ENGINE_MAX_ACTIVE);
   if (c.steps_per_epoch < 0 || c.items_per_thread < 0) return efail(PBN_ERR_INVALID, "negative tuning value");
+  if (!(c.epoch_target_ms >= 0.0)) return efail(PBN_ERR_INVALID, "epoch_target_ms %g", c.epoch_target_ms);
   if (c.threads_per_block && c.threads_per_block != 256 && c.threads_per_block != 512)
     return efail(PBN_ERR_INVALID, "threads_per_block must be 256 or 512");
   std::unique_ptr<pbn_engine> e(new pbn_engine());
@@ -831,10 +839,21 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
     if (q.phase == PH_DONE) continue;
     if (q.ch.length < q.target) {
       if (ntask >= e->cfg.max_active) continue;
-      const int64_t D = std::min<int64_t>(cand.S, q.target - q.ch.length);
-      if ((rc = reserve_bits(e, q, q.keep_from, q.ch.length + D))) { finish(e, q, rc); continue; }
       int gpb, staging;
       size_task(q, cand.threads, cand.ipt, gpb_cap, smem_cap, cand.big, &gpb, &staging);
+      int64_t D = std::min<int64_t>(cand.S, q.target - q.ch.length);
+      if (e->cfg.epoch_target_ms > 0 && e->items_per_ms > 0 && e->sim_ctas > 0) {
+        // each work item (gpb groups of this query on one CTA) takes at most
+        // about epoch_target_ms, so that queries arriving meanwhile wait at most
+        // that long for the next epoch: a CTA's step costs one round of its
+        // threads per `threads` items, at the rate the last epochs measured
+        const double round_ms = (double)cand.threads * e->sim_ctas / e->items_per_ms;
+        const double rounds = std::max(1.0, std::ceil((double)q.dev().n * gpb / cand.threads));
+        const int64_t cap =
+            std::max<int64_t>(kMinEpochSteps, (int64_t)(e->cfg.epoch_target_ms / (rounds * round_ms)));
+        D = std::min(D, cap);
+      }
+      if ((rc = reserve_bits(e, q, q.keep_from, q.ch.length + D))) { finish(e, q, rc); continue; }
       const int64_t groups_items = cdiv(q.G, gpb);
       if (nitems + groups_items > e->max_items) continue;   // next epoch
       SimArgs &a = e->h_tasks[ntask];
@@ -975,6 +994,11 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
     for (EQuery *q : e->epoch_queries) {
       q->batch_items += q->batch_items_epoch;
       sim_items += q->batch_items_epoch;
+    }
+    // the rate of epochs that keep every CTA busy (at least a few items per CTA)
+    if (sim_ms > 0.f && nitems >= 2 * e->sim_ctas) {
+      const double r = (double)sim_items / sim_ms;
+      e->items_per_ms = e->items_per_ms > 0 ? 0.7 * e->items_per_ms + 0.3 * r : r;
     }
   }
   {

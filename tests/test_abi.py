@@ -83,7 +83,7 @@ STRUCTS = {
                                          "sim_launches", "kernel_launches", "sim_items", "d2h_bytes", "apply_ms",
                                          "apply_launches"]),
     "EngineCfg": ("pbn_engine_cfg", ["hbm_budget_bytes", "max_active", "steps_per_epoch", "threads_per_block",
-                                     "items_per_thread", "use_graph"]),
+                                     "items_per_thread", "use_graph", "epoch_target_ms"]),
     "EngineQuery": ("pbn_engine_query", ["net", "method", "two_state", "skart", "tag"]),
     "EngineResult": ("pbn_engine_result", ["id", "tag", "method", "status", "two_state", "skart", "submit_epoch",
                                            "admit_epoch", "finish_epoch"]),

@@ -90,7 +90,8 @@ def test_mix_matches_alone(P, alone, use_graph):
 
 @pytest.mark.parametrize("cfg", [dict(steps_per_epoch=64, threads_per_block=256, items_per_thread=1),
                                  dict(steps_per_epoch=5000, threads_per_block=512, items_per_thread=8),
-                                 dict(steps_per_epoch=333, max_active=3)])
+                                 dict(steps_per_epoch=333, max_active=3),
+                                 dict(epoch_target_ms=0.3)])
 def test_tuning_does_not_change_results(P, alone, cfg):
     eng = P.Engine(**cfg)
     nets = {}
@@ -328,7 +329,7 @@ def test_serving_pool_continuous_mix():
             return dict(base, r=r)
         return dict(base, H_star=r, relative=False)
 
-    eng = P.Engine(use_graph=True)
+    eng = P.Engine(use_graph=True, epoch_target_ms=2.0)
     results, nxt = [], 0
     for _ in range(100_000):
         for _ in range(3):
