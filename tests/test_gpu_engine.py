@@ -180,8 +180,10 @@ def _cmp_oracle(kind, g, o, what):
         for k in ("psi", "length", "kappa", "batches", "spacer", "sample_size", "gr_rounds", "rand_rounds",
                   "ci_rounds"):
             assert g[k] == o[k], (what, k, g[k], o[k])
-        for k in ("mean", "ci_lo", "ci_hi", "H", "var", "skew", "phi"):
-            assert g[k] == pytest.approx(o[k], rel=1e-10, abs=1e-13), (what, k)
+        for k in ("mean", "ci_lo", "ci_hi", "H", "var"):
+            assert g[k] == pytest.approx(o[k], rel=1e-12, abs=1e-15), (what, k)
+        for k in ("skew", "phi"):
+            assert g[k] == pytest.approx(o[k], rel=0, abs=1e-12), (what, k)
 
 
 def test_mix_matches_oracle(P):

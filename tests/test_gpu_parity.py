@@ -6,8 +6,10 @@ sums).  FP64 statistics: R-hat, alpha, beta to 1e-12 relative (both sides
 form them from the same integers; alpha and beta are single correctly
 rounded divisions and must agree exactly), M and N exactly unless the value
 before ceil lies within 1e-12 relative of an integer, Skart statistics to
-1e-10 relative (moments are formed differently on the two sides: exact
-shifted integer moments on the GPU, two-pass FP64 over means in the oracle).
+1e-12 (relative for the mean, variance and interval, absolute for the
+skewness and lag-1 correlation; moments are formed differently on the two
+sides: exact shifted integer moments on the GPU, two-pass FP64 over means in
+the oracle).
 """
 import math
 
@@ -310,8 +312,13 @@ def test_estimate_skart_matches_oracle(P, case):
     g = P.pbn_estimate_skart(P.pbn_load(net), soi, seed=5, alpha=0.05, **kw)
     for k in ("psi", "length", "kappa", "batches", "spacer", "sample_size", "gr_rounds", "rand_rounds", "ci_rounds"):
         assert g[k] == o[k], k
-    for k in ("mean", "ci_lo", "ci_hi", "H", "var", "skew", "phi"):
-        assert g[k] == pytest.approx(o[k], rel=1e-10, abs=1e-13), k
+    # mean, variance, CI and half-width to 1e-12 relative; skewness and lag-1
+    # correlation to 1e-12 absolute (their relative error grows where they are
+    # near 0: both sides reach them through cancelling central-moment sums)
+    for k in ("mean", "ci_lo", "ci_hi", "H", "var"):
+        assert g[k] == pytest.approx(o[k], rel=1e-12, abs=1e-15), k
+    for k in ("skew", "phi"):
+        assert g[k] == pytest.approx(o[k], rel=0, abs=1e-12), k
 
 
 def _tiles(net):
