@@ -63,6 +63,8 @@ constexpr int kReqBlocks = 64;   // most virtual blocks of one statistics reques
 // With a latency bound (pbn_engine_cfg.epoch_target_ms) an epoch's extension
 // of a query is never below kMinEpochSteps transitions.
 constexpr int64_t kMinEpochSteps = 64;
+// At most this many queries to extend in an epoch for the light-load path.
+constexpr int kAloneMax = 4;
 constexpr int kCounters = 8;     // items, next item, virtual blocks, next virtual block, requests
 
 // ------------------------------------------------------------------ kernels
@@ -822,9 +824,19 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
   // spread light epochs: at least about two CTAs per SM when the active
   // chain groups allow it
   int64_t total_groups = 0;
+  int nsim = 0;
   for (auto &qp : e->active)
-    if (qp->phase != PH_DONE && qp->ch.length < qp->target) total_groups += qp->G;
+    if (qp->phase != PH_DONE && qp->ch.length < qp->target) {
+      total_groups += qp->G;
+      nsim++;
+    }
   const int gpb_cap = (int)std::max<int64_t>(1, total_groups / (2 * (int64_t)e->sms));
+  // light load (a few queries to extend, none waiting for admission): queries
+  // with few chain groups are extended outside the batched kernel, one after
+  // another, by the schedule pbn_run_chains picks (select-ahead for them: the
+  // batched fused kernel would leave most SMs idle and wait on its Philox
+  // rounds every step); the same chains, bit for bit
+  const bool few = nsim <= kAloneMax && e->pending.empty();
   int ntask = 0, nitems = 0, nreq = 0, vblocks = 0;
   size_t smem = 0;
   int64_t updates = 0;
@@ -842,7 +854,8 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       int gpb, staging;
       size_task(q, cand.threads, cand.ipt, gpb_cap, smem_cap, cand.big, &gpb, &staging);
       int64_t D = std::min<int64_t>(cand.S, q.target - q.ch.length);
-      if (e->cfg.epoch_target_ms > 0 && e->items_per_ms > 0 && e->sim_ctas > 0) {
+      const bool alone_ok = few && 2 * q.G <= e->sms;
+      if (e->cfg.epoch_target_ms > 0 && !alone_ok && e->items_per_ms > 0 && e->sim_ctas > 0) {
         // each work item (gpb groups of this query on one CTA) takes at most
         // about epoch_target_ms, so that queries arriving meanwhile wait at most
         // that long for the next epoch: a CTA's step costs one round of its
@@ -921,12 +934,41 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       q.req = nreq++;
     }
   }
+  ECUDA(cudaEventRecord(e->e0, e->s), "event");
+  // the light-load path (see `few`); a task it cannot take stays batched.
+  // Not a tuning sample.
+  std::vector<char> alone_task(ntask, 0);
+  int nalone = 0;
+  for (int t = 0; t < ntask && few; t++) {
+    EQuery &q = *e->epoch_queries[t];
+    if (!(2 * q.G <= e->sms && q.sim_D > 0)) continue;
+    pbn_run_cfg rc_cfg;
+    memset(&rc_cfg, 0, sizeof rc_cfg);
+    rc_cfg.seed = q.seed;
+    rc_cfg.perturb_mode = q.mode;
+    rc_cfg.soi.size = (int32_t)q.soi_nodes.size();
+    rc_cfg.soi.nodes = q.soi_nodes.data();
+    rc_cfg.soi.values = q.soi_vals.data();
+    pbn_chains c = q.ch;  // q.ch.length advances when the epoch is applied
+    int64_t l = 0;
+    if (run_chains_alone(q.dev(), rc_cfg, c, q.sim_D, e->s, e->status, &l) == PBN_OK) {
+      alone_task[t] = 1;
+      nalone++;
+      nitems -= (int)cdiv(q.G, e->h_tasks[t].gpb);
+      q.batch_items_epoch = 0;
+      launches += (int)l;
+    } else {
+      set_last_error("");  // fall back to the batched kernel
+    }
+  }
+  const bool alone = nalone > 0;
   // items, longest tasks first
   std::sort(order.begin(), order.end());
   {
     int k = 0;
     for (auto &o : order) {
       const int t = o.second;
+      if (alone_task[t]) continue;
       const int gpb = task_groups[t].second;
       const int G = e->h_tasks[t].G;
       for (int g0 = 0; g0 < G; g0 += gpb) {
@@ -935,34 +977,6 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
         it.g0 = g0;
         it.ngl = std::min(gpb, G - g0);
         it.pad = 0;
-      }
-    }
-  }
-  ECUDA(cudaEventRecord(e->e0, e->s), "event");
-  // A lone query with few chain groups, nothing waiting for admission: the
-  // batched fused kernel would leave most SMs idle and wait on its Philox
-  // rounds every step, so its extension runs alone with the schedule
-  // pbn_run_chains picks (the same chains, bit for bit); the statistics stay
-  // in the batched launch.  Not a tuning sample.
-  bool alone = false;
-  if (ntask == 1 && e->pending.empty()) {
-    EQuery &q = *e->epoch_queries[0];
-    if (2 * q.G <= e->sms && q.sim_D > 0) {
-      pbn_run_cfg rc_cfg;
-      memset(&rc_cfg, 0, sizeof rc_cfg);
-      rc_cfg.seed = q.seed;
-      rc_cfg.perturb_mode = q.mode;
-      rc_cfg.soi.size = (int32_t)q.soi_nodes.size();
-      rc_cfg.soi.nodes = q.soi_nodes.data();
-      rc_cfg.soi.values = q.soi_vals.data();
-      pbn_chains c = q.ch;  // q.ch.length advances when the epoch is applied
-      int64_t l = 0;
-      if (run_chains_alone(q.dev(), rc_cfg, c, q.sim_D, e->s, e->status, &l) == PBN_OK) {
-        alone = true;
-        nitems = 0;
-        launches += (int)l;
-      } else {
-        set_last_error("");  // fall back to the batched kernel
       }
     }
   }
