@@ -405,6 +405,9 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
   const int sub = lane & (T - 1);
   const int slot = threadIdx.x / T;
   const int nslots = blockDim.x / T;
+  const int dr = nslots / gpb, dgl = nslots - dr * gpb;
+  // valid lanes: every group but the last is full
+  const uint32_t last_g = (uint32_t)((a.omega - 1) / 32), last_mask = lane_mask(a.omega, last_g);
   uint32_t *cur = bufA, *nxt = bufB;
   for (int s = 0; s < nsteps; s++) {
     ItemCtx c;
@@ -437,19 +440,29 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
         p1 = a.tiles[t + 1];
         c.fn_s = tilebuf[u & 1] - node_f0(node_s[p0]);
       }
+      // item q = base + slot is (node position r, group gl) with q = r gpb + gl;
+      // (r, gl) advance by (nslots / gpb, nslots % gpb) per round, so no
+      // division runs per item
+      int r = (p0 * gpb + slot) / gpb;
+      int gl = (p0 * gpb + slot) - r * gpb;
       for (int base = p0 * gpb; base < p1 * gpb; base += nslots) {  // uniform trip count
         const int q = base + slot;
-        const int r = q / gpb;
-        c.gl = q - r * gpb;
+        c.gl = gl;
         c.active = (q < p1 * gpb) && (c.gl < ngl);
         const uint32_t rec = c.active ? node_s[r] : 0u;
         c.L = c.active ? node_l(rec) : 0;
         c.i = node_id(rec);
         c.f0 = node_f0(rec);
         c.g = g0 + (uint32_t)c.gl;
-        c.vmask = c.active ? lane_mask(a.omega, c.g) : 0u;
+        c.vmask = c.active ? (c.g == last_g ? last_mask : kFull) : 0u;
         const int LW = (int)__reduce_max_sync(kFull, (unsigned)c.L);
         dispatch_item<MODE, T, BPR, WIDE, LMAX>(LW, rk, P32, c);
+        r += dr;
+        gl += dgl;
+        if (gl >= gpb) {
+          gl -= gpb;
+          r++;
+        }
       }
       __syncthreads();
       if (staging == STAGE_TILES && threadIdx.x == 0) {
