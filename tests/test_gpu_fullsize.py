@@ -109,3 +109,46 @@ def test_mid_workload_schedules_sampled_chains(P, schedule):
     net, soi, cfg = S.mid_config()
     rng = np.random.default_rng(3)
     _replay_and_compare(P, net, soi, cfg["omega"], 4242, 2500, rng, k=2, schedule=schedule)
+
+
+def test_large_network_skart_several_batches_per_chain(P):
+    """Alg. GR + Alg. 4 on the large network (n = 2000 scale-free) with 256
+    chains, so that every chain holds several batches (p = ceil(p/omega)
+    omega from 1280) and the randomness test and the lag-1 factor act on
+    within-chain neighbours at this size.  The chains are replayed to the
+    query's final length; the oracle's batch-means statistics on the
+    replayed bitstream give the report's mean, variance, interval and
+    half-width (1e-12 relative; skewness and correlation 1e-12 absolute), the
+    randomness test passes on the accepted layout, and sampled chains match
+    the oracle chain by chain."""
+    net, nodes, cfg = S.large_config()
+    st, _ = oracle.simulate(net, 0, 5, oracle.init_states(net, 5, 1), 0, 1024, None, record=False)
+    soi = S.StateOfInterest(nodes[:2], st[0][nodes[:2]])
+    N = P.pbn_load(net)
+    omega, seed = 256, 11
+    sk = P.pbn_estimate_skart(N, soi, omega=omega, seed=seed, H_star=0.05, relative=True, alpha=0.05, psi0=256,
+                              rhat=1.05, max_length=1 << 18)
+    bpc = sk["batches"] // omega
+    assert bpc >= 2 and sk["batches"] % omega == 0
+    kappa, start, L = sk["kappa"], sk["psi"], sk["length"]
+    cs = P.ChainSet(N, omega, bits_cap=L)
+    P.pbn_init_chains(cs, seed)
+    P.pbn_run_chains(cs, L, seed, P.PER_NODE, soi)
+    x = cs.indicator_numpy(start, kappa * bpc)
+    means = x.reshape(omega, bpc, kappa).mean(axis=2).reshape(-1)
+    ci = oracle.skart_ci(means, omega, bpc, 0.05)
+    for k in ("mean", "var", "ci_lo", "ci_hi", "H"):
+        assert sk[k] == pytest.approx(ci[k], rel=1e-12, abs=1e-15), k
+    for k in ("skew", "phi"):
+        assert sk[k] == pytest.approx(ci[k], rel=0, abs=1e-12), k
+    if sk["ci_rounds"] == 1:
+        # the interval was taken on the layout the randomness test accepted
+        spaced_ok, _ = oracle.vonneumann_pass(means, omega, bpc, sk["spacer"], 0.2)
+        assert spaced_ok
+    states = cs.states_numpy()
+    full = cs.indicator_numpy(0, L)
+    for c in (0, 137, omega - 1):
+        st0 = oracle.init_states(net, seed, 1, chain0=c)
+        ref, ind = oracle.simulate(net, 0, seed, st0, 0, L, soi, chain0=c)
+        assert np.array_equal(states[c], ref[0]), c
+        assert np.array_equal(full[c], ind[0]), c
