@@ -67,15 +67,17 @@ __device__ __noinline__ void select_item_wide(const RoundKeys &rk, uint32_t P32,
 // mostly share one node shape (processing order groups shapes).
 template <int MODE, int BPR>
 __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ SimArgs a) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)a.steps * a.G * a.n;
+  // 32-bit index arithmetic: the launcher keeps steps x G x n below 2^32
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t total = (uint32_t)a.steps * (uint32_t)a.G * (uint32_t)a.n;
   const bool active = q < total;
-  const int64_t sg = active ? q / a.n : 0;
-  const int r = active ? (int)(q - sg * a.n) : 0;
-  const int s = (int)(sg / a.G);
+  const uint32_t sg = active ? q / (uint32_t)a.n : 0u;
+  const int r = active ? (int)(q - sg * (uint32_t)a.n) : 0;
+  const uint32_t su = sg / (uint32_t)a.G;
+  const int s = (int)su;
   ItemCtx c;
   c.fn_s = a.fn;
-  c.g = (uint32_t)(sg - (int64_t)s * a.G);
+  c.g = sg - su * (uint32_t)a.G;
   const uint32_t rec = active ? a.node[r] : 0u;
   c.L = active ? node_l(rec) : 0;
   c.i = node_id(rec);
@@ -455,14 +457,17 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
       flush(done, a.steps - done);
     }
   } else {
+    const int dit = (int)blockDim.x / T, dr = dit / gpb, dgl = dit - dr * gpb;
     for (int s = 0; s < kRing - 1; s++) issue(s);
     for (int s = 0; s < a.steps; s++) {
       step_top(s);
       const uint32_t *slot = ring + (size_t)(s % kRing) * gpb * W;
+      // item it = r gpb + gl of thread q = it T + sub; (r, gl) advance by the
+      // CTA's items per round without a division per item
+      int r = (int)(threadIdx.x / T) / gpb, gl = (int)(threadIdx.x / T) - r * gpb;
       for (int base = 0; base < items * T; base += blockDim.x) {  // uniform trip count
         const int q = base + threadIdx.x;
         const int it = q / T, sub = q & (T - 1);
-        const int r = it / gpb, gl = it - r * gpb;
         const bool active = it < items && gl < ngl;
         const uint32_t rec = active ? node_s[r] : 0u;
         const int L = active ? node_l(rec) : 0;
@@ -474,6 +479,12 @@ __global__ void __launch_bounds__(apply_max_threads<T>(), 1) apply_kernel(const 
         uint32_t fword = 0u;
         eval_rest(0, LW, L, f0, gl, sub, w, rest, fword);
         if (active && sub == 0) finish(node_id(rec) * gpb + gl, gl, P, fword, slot);
+        r += dr;
+        gl += dgl;
+        if (gl >= gpb) {
+          gl -= gpb;
+          r++;
+        }
       }
       uint32_t *tmp = cur;
       cur = nxt;
@@ -922,7 +933,7 @@ static cudaError_t launch_select_variant(const SimArgs &a, size_t pad, cudaStrea
   const int64_t total = (int64_t)a.steps * a.G * a.n;
   const int threads = 256;
   const int64_t blocks = (total + threads - 1) / threads;
-  if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  if (total >= (int64_t)1 << 32) return cudaErrorInvalidValue;  // the kernel indexes items in 32 bits
   static bool attr = false;
   if (pad > 0 && !attr) {
     cudaError_t e = cudaFuncSetAttribute(select_kernel<MODE, BPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
