@@ -60,6 +60,9 @@ union ReqOut {
 };
 
 constexpr int kReqBlocks = 64;   // most virtual blocks of one statistics request
+// Statistics requests per query and epoch: a two-state query at its Gelman &
+// Rubin check also asks for the first two-state counts of the same window.
+constexpr int kReqPerQuery = 2;
 // With a latency bound (pbn_engine_cfg.epoch_target_ms) an epoch's extension
 // of a query is never below kMinEpochSteps transitions.
 constexpr int64_t kMinEpochSteps = 64;
@@ -257,7 +260,7 @@ struct EQuery {
   int phase = PH_GR;
   int64_t psi = 0, target = 0, keep_from = 0;
   int64_t sim_D = 0;
-  int req = -1;
+  int req = -1, req2 = -1;
   // Skart
   int64_t start = 0, eta = 0, kappa = 1, p = 0, d = 0;
   pbn_two_state_report tr;
@@ -610,14 +613,16 @@ int capture_graph(pbn_engine *e, int threads, size_t smem) {
   ECUDA(cudaStreamBeginCapture(e->s, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaMemcpyAsync(e->d_tasks, e->h_tasks, sizeof(SimArgs) * e->cfg.max_active, cudaMemcpyHostToDevice, e->s);
   cudaMemcpyAsync(e->d_items, e->h_items, sizeof(BatchItem) * e->max_items, cudaMemcpyHostToDevice, e->s);
-  cudaMemcpyAsync(e->d_reqs, e->h_reqs, sizeof(StatReq) * e->cfg.max_active, cudaMemcpyHostToDevice, e->s);
+  cudaMemcpyAsync(e->d_reqs, e->h_reqs, sizeof(StatReq) * kReqPerQuery * e->cfg.max_active, cudaMemcpyHostToDevice,
+                  e->s);
   cudaMemcpyAsync(e->d_cnt, e->h_cnt, sizeof(int) * kCounters, cudaMemcpyHostToDevice, e->s);
   // timing events of the simulation launch, kept in the graph as event nodes
   cudaEventRecordWithFlags(e->es0, e->s, cudaEventRecordExternal);
   batch_sim_kernel<<<sim_blocks, threads, gsmem, e->s>>>(e->d_tasks, e->d_items, e->d_cnt);
   cudaEventRecordWithFlags(e->es1, e->s, cudaEventRecordExternal);
   batch_stats_kernel<<<e->sms, 256, 0, e->s>>>(e->d_reqs, e->d_cnt, e->d_partials, e->d_tickets, e->d_out);
-  cudaMemcpyAsync(e->h_out, e->d_out, sizeof(ReqOut) * e->cfg.max_active, cudaMemcpyDeviceToHost, e->s);
+  cudaMemcpyAsync(e->h_out, e->d_out, sizeof(ReqOut) * kReqPerQuery * e->cfg.max_active, cudaMemcpyDeviceToHost,
+                  e->s);
   ECUDA(cudaStreamEndCapture(e->s, &g), "end capture");
   cudaError_t err = cudaGraphInstantiate(&e->exec, g, 0);
   cudaGraphDestroy(g);
@@ -686,13 +691,14 @@ extern "C" int pbn_engine_create(const pbn_engine_cfg *cfg, void *stream, pbn_en
   ECUDA(cudaMallocHost(&e->h_items, sizeof(BatchItem) * e->max_items), "engine alloc");
   ECUDA(cudaMalloc(&e->d_cnt, sizeof(int) * kCounters), "engine alloc");
   ECUDA(cudaMallocHost(&e->h_cnt, sizeof(int) * kCounters), "engine alloc");
-  ECUDA(cudaMalloc(&e->d_reqs, sizeof(StatReq) * A), "engine alloc");
-  ECUDA(cudaMallocHost(&e->h_reqs, sizeof(StatReq) * A), "engine alloc");
-  ECUDA(cudaMalloc(&e->d_out, sizeof(ReqOut) * A), "engine alloc");
-  ECUDA(cudaMallocHost(&e->h_out, sizeof(ReqOut) * A), "engine alloc");
-  ECUDA(cudaMalloc(&e->d_partials, sizeof(unsigned long long) * A * kReqBlocks * 4), "engine alloc");
-  ECUDA(cudaMalloc(&e->d_tickets, sizeof(unsigned int) * A), "engine alloc");
-  ECUDA(cudaMemsetAsync(e->d_tickets, 0, sizeof(unsigned int) * A, e->s), "engine memset");
+  const int AR = kReqPerQuery * A;  // statistics requests of one epoch
+  ECUDA(cudaMalloc(&e->d_reqs, sizeof(StatReq) * AR), "engine alloc");
+  ECUDA(cudaMallocHost(&e->h_reqs, sizeof(StatReq) * AR), "engine alloc");
+  ECUDA(cudaMalloc(&e->d_out, sizeof(ReqOut) * AR), "engine alloc");
+  ECUDA(cudaMallocHost(&e->h_out, sizeof(ReqOut) * AR), "engine alloc");
+  ECUDA(cudaMalloc(&e->d_partials, sizeof(unsigned long long) * AR * kReqBlocks * 4), "engine alloc");
+  ECUDA(cudaMalloc(&e->d_tickets, sizeof(unsigned int) * AR), "engine alloc");
+  ECUDA(cudaMemsetAsync(e->d_tickets, 0, sizeof(unsigned int) * AR, e->s), "engine memset");
   ECUDA(scratch_init(e->sk, e->s), "engine scratch");
   ECUDA(cudaMalloc(&e->d_sk, sizeof(pbn_skart_result)), "engine alloc");
   ECUDA(cudaMallocHost(&e->h_sk, sizeof(pbn_skart_result)), "engine alloc");
@@ -704,7 +710,7 @@ extern "C" int pbn_engine_create(const pbn_engine_cfg *cfg, void *stream, pbn_en
   ECUDA(cudaMemsetAsync(e->status, 0, sizeof(int), e->s), "engine memset");
   memset(e->h_tasks, 0, sizeof(SimArgs) * A);
   memset(e->h_items, 0, sizeof(BatchItem) * e->max_items);
-  memset(e->h_reqs, 0, sizeof(StatReq) * A);
+  memset(e->h_reqs, 0, sizeof(StatReq) * AR);
   memset(e->h_cnt, 0, sizeof(int) * kCounters);
   ECUDA(cudaFuncSetAttribute(batch_sim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit()), "smem attr");
   // candidates of the autotuner (a fixed setting leaves one candidate)
@@ -847,6 +853,7 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
     EQuery &q = *qp;
     q.sim_D = 0;
     q.req = -1;
+    q.req2 = -1;
     q.batch_items_epoch = 0;
     if (q.phase == PH_DONE) continue;
     if (q.ch.length < q.target) {
@@ -932,6 +939,17 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       r.block0 = vblocks;
       vblocks += r.nblocks;
       q.req = nreq++;
+      if (q.phase == PH_GR && q.method == PBN_METHOD_TWO_STATE) {
+        // Alg. 3's first check counts the same window [psi, 2 psi) the
+        // Gelman & Rubin check reads: asked for now, used if R-hat converges
+        // (as pbn_estimate_two_state does), so the query needs no epoch of its own for it
+        StatReq &t = e->h_reqs[nreq];
+        t = r;
+        t.kind = REQ_TS;
+        t.block0 = vblocks;
+        vblocks += t.nblocks;
+        q.req2 = nreq++;
+      }
     }
   }
   ECUDA(cudaEventRecord(e->e0, e->s), "event");
@@ -991,7 +1009,7 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
       if ((rc = capture_graph(e, cand.threads, smem))) return rc;
       ECUDA(cudaGraphLaunch(e->exec, e->s), "graph launch");
       launches += 2;
-      d2h += (int64_t)sizeof(ReqOut) * e->cfg.max_active;
+      d2h += (int64_t)sizeof(ReqOut) * kReqPerQuery * e->cfg.max_active;
     } else {
       if ((rc = launch_direct(e, cand.threads, smem, ntask, nitems, nreq))) return rc;
       launches += (nitems ? 1 : 0) + (nreq ? 1 : 0);
@@ -1034,8 +1052,13 @@ extern "C" int pbn_engine_step(pbn_engine *e, pbn_engine_stats *st) {
     if (q.phase == PH_DONE) continue;
     q.ch.length += q.sim_D;
     if (q.req >= 0) {
-      if (q.phase == PH_GR) ts_after_gr(e, q, e->h_out[q.req].gr);
-      else ts_after_counts(e, q, e->h_out[q.req].ts);
+      if (q.phase == PH_GR) {
+        ts_after_gr(e, q, e->h_out[q.req].gr);
+        // converged: the first two-state check's window is the one counted
+        if (q.req2 >= 0 && q.phase == PH_TS && q.target == q.ch.length) ts_after_counts(e, q, e->h_out[q.req2].ts);
+      } else {
+        ts_after_counts(e, q, e->h_out[q.req].ts);
+      }
     }
   }
   for (auto &qp : e->active) {
