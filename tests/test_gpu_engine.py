@@ -260,12 +260,13 @@ def _replay_window(P, net, soi, omega, seed, rep, rng, mode=0):
         assert np.array_equal(x[c], ind[0][psi:]), c
 
 
-def test_batch_workload_in_mix_equals_alone_and_replays():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_workload_in_mix_equals_alone_and_replays(mode):
     """The batched workload's 64 networks (n log-uniform in [50, 3000],
-    256-4096 chains, p in {0.001, 0.01}, two-state r = 0.005) in one engine:
-    every query equals its single-query run; for the networks of n >= 2000
-    the chains replayed to the query's final length give its counts, and
-    sampled chains match the oracle."""
+    256-4096 chains, p in {0.001, 0.01}, two-state r = 0.005) in one engine,
+    under both perturbation readings: every query equals its single-query
+    run; for the networks of n >= 2000 the chains replayed to the query's
+    final length give its counts, and sampled chains match the oracle."""
     from paper_1508_07828_gb300 import _build
     _build.build()
     import paper_1508_07828_gb300 as P
@@ -273,7 +274,7 @@ def test_batch_workload_in_mix_equals_alone_and_replays():
     assert len(cfgs) == 64 and max(net.n for net, _, _ in cfgs) >= 2000
     nets = [P.pbn_load(net) for net, _, _ in cfgs]
     kw = lambda c, k: dict(omega=c["omega"], seed=1000 + k, psi0=1024, rhat=c["rhat"], eps=c["eps"], r=c["r"],
-                           s=c["s"], max_length=1 << 20)
+                           s=c["s"], max_length=1 << 20, mode=mode)
     eng = P.Engine(use_graph=True)
     for k, ((net, soi, c), N) in enumerate(zip(cfgs, nets)):
         eng.submit_two_state(N, soi, tag=k, **kw(c, k))
@@ -288,7 +289,7 @@ def test_batch_workload_in_mix_equals_alone_and_replays():
         for key in TS_KEYS:
             assert got["report"][key] == ref[key], (k, key)
         if net.n >= 2000:
-            _replay_window(P, net, soi, c["omega"], 1000 + k, got["report"], rng)
+            _replay_window(P, net, soi, c["omega"], 1000 + k, got["report"], rng, mode=mode)
             replayed += 1
     assert replayed >= 2
 
