@@ -104,3 +104,20 @@ def test_sweep_sized_dense_model_sampled_chains(P):
         ref, ind = oracle.simulate(net, 0, seed, st0, 0, steps, soi, chain0=c)
         assert np.array_equal(states[c], ref[0]), c
         assert np.array_equal(bits[c], ind[0]), c
+
+
+@pytest.mark.parametrize("staging", ["tiles", "global"])
+def test_dense_staging_modes_bit_exact(P, staging):
+    """The dense variant with its function records streamed through shared
+    memory as TMA tiles (several per step) or read from global memory: the
+    same chains as the oracle."""
+    net, soi = S.sweep_config(200, "dense")
+    assert net.n_functions > 1536  # more than one tile of records
+    N = P.pbn_load(net)
+    omega, steps, seed = 64, 9, 515
+    cs = P.ChainSet(N, omega, bits_cap=steps)
+    P.pbn_init_chains(cs, seed)
+    P.pbn_run_chains(cs, steps, seed, P.PER_NODE, soi, staging=staging)
+    ref, ind = oracle.simulate(net, 0, seed, oracle.init_states(net, seed, omega), 0, steps, soi)
+    assert np.array_equal(cs.states_numpy(), ref)
+    assert np.array_equal(cs.indicator_numpy(0, steps), ind)
