@@ -155,6 +155,10 @@ cudaError_t launch_init(const NetDev &net, uint64_t seed, uint32_t *state, int64
 // thread per round (T = 1: 1 or 2; T = 2 uses 2; T = 4 uses 1).
 cudaError_t launch_sim(const SimArgs &a, int mode, int T, int BPR, int threads, size_t smem, cudaStream_t s);
 size_t sim_smem_bytes(int n, int F, int gpb, int mode, int staging, int tile_bytes);
+// Dynamic shared memory a simulation or apply launch may use: the device's
+// per-block opt-in limit less kStaticSmemReserve, which covers the kernels'
+// static shared memory (the CTA body's 256-byte nibble table).
+constexpr int kStaticSmemReserve = 1024;
 // Select-ahead schedule (pbn_split.cu): the category words of a.steps steps
 // of all groups, then their application (a.staging: STAGE_SMEM or STAGE_GLOBAL).
 // pad: unused dynamic shared memory per block (placement only; 0 = none).

@@ -103,6 +103,7 @@ int sim_max_smem() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) v = 48 * 1024;
+    v -= kStaticSmemReserve;
   }
   return v;
 }

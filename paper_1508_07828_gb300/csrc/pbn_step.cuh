@@ -111,13 +111,25 @@ struct ItemCtx {
   uint32_t vmask;
   uint64_t t;
   int sub;
+  const uint4 *nib;  // nibble v -> its four bits, most significant first, as 0 / ~0 masks (shared memory)
 };
+
+// The table ItemCtx::nib points to: one CTA's 16 entries, thread v < 16 fills
+// entry v.
+__device__ __forceinline__ void fill_nibble_masks(uint4 *nib) {
+  if (threadIdx.x < 16) {
+    const uint32_t v = threadIdx.x;
+    nib[v] = make_uint4(0u - ((v >> 3) & 1u), 0u - ((v >> 2) & 1u), 0u - ((v >> 1) & 1u), 0u - (v & 1u));
+  }
+}
 
 // Category draw of one item of one transition with LW (warp-uniform)
 // category bounds; bound 0 is P32, bound m is T_{m-1}; bounds m >= L are
 // unreachable (all lanes below).  On return lt[m] holds the lanes whose
 // uniform lies below bound m (complete in every one of the T threads).
-template <int LW, int T, int BPR>
+// NIB: the bound's four digits of a block come as 0 / ~0 masks from the
+// nibble table c.nib (one shared load) instead of being spread bit by bit.
+template <int LW, int T, int BPR, bool NIB = false>
 __device__ __forceinline__ void draw_below(const RoundKeys &rk, uint32_t P32, const ItemCtx &c, uint32_t (&lt)[LW]) {
   uint32_t ts[LW], und[LW];
 #pragma unroll
@@ -147,11 +159,23 @@ __device__ __forceinline__ void draw_below(const RoundKeys &rk, uint32_t P32, co
       const uint32_t Rq[4] = {R.x, R.y, R.z, R.w};
 #pragma unroll
       for (int m = 0; m < LW; m++) {
-        const uint32_t tsb = ts[m] << (4u * b);
+        // the bound's digits 4b .. 4b+3 as 0 / ~0
+        uint32_t tmq[4];
+        if (NIB) {
+          const uint4 nm = c.nib[(ts[m] >> (28u - 4u * b)) & 0xFu];
+          tmq[0] = nm.x;
+          tmq[1] = nm.y;
+          tmq[2] = nm.z;
+          tmq[3] = nm.w;
+        } else {
+          const uint32_t tsb = ts[m] << (4u * b);
+#pragma unroll
+          for (int q = 0; q < 4; q++) tmq[q] = (uint32_t)((int32_t)(tsb << q) >> 31);
+        }
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-          // bound digit as 0 / ~0; lanes whose digit differs are decided
-          const uint32_t tm = (uint32_t)((int32_t)(tsb << q) >> 31);
+          // lanes whose digit differs from the bound's are decided
+          const uint32_t tm = tmq[q];
           const uint32_t dec = u[m] & (Rq[q] ^ tm);
           l[m] |= dec & tm;  // bound digit 1, lane digit 0: u < bound
           u[m] &= ~dec;
@@ -199,7 +223,7 @@ __device__ __forceinline__ void select_masks(const uint32_t (&lt)[LW], uint32_t 
 template <int LW, int MODE, int T, int BPR, bool WIDE, int KMAX = kWideK>
 __device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, const ItemCtx &c) {
   uint32_t lt[LW];
-  draw_below<LW, T, BPR>(rk, P32, c, lt);
+  draw_below<LW, T, BPR, true>(rk, P32, c, lt);
   uint32_t sel[LW];
   select_masks<LW>(lt, c.vmask, sel);
   uint32_t fword = 0u;
@@ -374,6 +398,8 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
   }
   if (MODE == PBN_PERTURB_GLOBAL)
     for (int j = threadIdx.x; j < 2 * gpb; j += blockDim.x) anyP[j] = 0u;
+  __shared__ uint4 s_nib[16];
+  fill_nibble_masks(s_nib);
   const int ntiles = staging == STAGE_TILES ? a.ntiles : 1;
   const int64_t total_tiles = (int64_t)nsteps * ntiles;
   if (staging == STAGE_TILES && threadIdx.x == 0) {
@@ -421,6 +447,7 @@ __device__ __forceinline__ void cta_simulate(const SimArgs &a, const RoundKeys &
     c.gpb = gpb;
     c.t = a.t0 + (uint64_t)(soff + s);
     c.sub = sub;
+    c.nib = s_nib;
     for (int t = 0; t < ntiles; t++) {
       int p0 = 0, p1 = n;
       c.fn_s = fn_s;
