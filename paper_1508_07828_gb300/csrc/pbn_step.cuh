@@ -35,11 +35,38 @@ __device__ __forceinline__ uint32_t eval_tt(uint32_t tt, const uint32_t *x) {
   }
 }
 
+// The same tree with its leaves taken four at a time from the nibble table
+// (nib[v] = bits 3, 2, 1, 0 of v as 0 / ~0 masks): one shared load per four
+// leaves instead of two shifts per leaf.  The apply kernels of the
+// select-ahead schedule keep eval_tt.
+template <int K>
+__device__ __forceinline__ uint32_t eval_tt_nib(uint32_t tt, const uint32_t *x, const uint4 *nib) {
+  if constexpr (K < 2) {
+    return eval_tt<K>(tt, x);
+  } else {
+    constexpr int NL = 1 << K;
+    uint32_t v[NL / 2];
+#pragma unroll
+    for (int j = 0; j < NL / 4; j++) {
+      const uint4 nm = nib[(tt >> (4 * j)) & 0xFu];
+      v[2 * j] = (x[0] & nm.z) | (~x[0] & nm.w);
+      v[2 * j + 1] = (x[0] & nm.x) | (~x[0] & nm.y);
+    }
+#pragma unroll
+    for (int m = 1; m < K; m++) {
+#pragma unroll
+      for (int q = 0; q < (NL >> (m + 1)); q++) v[q] = (x[m] & v[2 * q + 1]) | (~x[m] & v[2 * q]);
+    }
+    return v[0];
+  }
+}
+
 // Function record evaluated at tree depth K >= its own k: the truth table is
 // replicated to 2^K leaves; parents m >= k are node 0 (their value then does
 // not matter).
 template <int K>
-__device__ __forceinline__ uint32_t eval_at_depth(uint4 rec, int k, const uint32_t *cur, int gpb, int gl) {
+__device__ __forceinline__ uint32_t eval_at_depth(uint4 rec, int k, const uint32_t *cur, int gpb, int gl,
+                                                 const uint4 *nib) {
   uint32_t tt = rec.x;
 #pragma unroll
   for (int e = 0; e < K; e++)
@@ -53,18 +80,19 @@ __device__ __forceinline__ uint32_t eval_at_depth(uint4 rec, int k, const uint32
   uint32_t x[5];
 #pragma unroll
   for (int m = 0; m < K; m++) x[m] = cur[p[m] * gpb + gl];
-  return eval_tt<K>(tt, x);
+  return eval_tt_nib<K>(tt, x, nib);
 }
 
 // K is warp-uniform, so the switch does not diverge.
-__device__ __forceinline__ uint32_t eval_uniform(int K, uint4 rec, int k, const uint32_t *cur, int gpb, int gl) {
+__device__ __forceinline__ uint32_t eval_uniform(int K, uint4 rec, int k, const uint32_t *cur, int gpb, int gl,
+                                                const uint4 *nib) {
   switch (K) {
-    case 0: return eval_at_depth<0>(rec, k, cur, gpb, gl);
-    case 1: return eval_at_depth<1>(rec, k, cur, gpb, gl);
-    case 2: return eval_at_depth<2>(rec, k, cur, gpb, gl);
-    case 3: return eval_at_depth<3>(rec, k, cur, gpb, gl);
-    case 4: return eval_at_depth<4>(rec, k, cur, gpb, gl);
-    default: return eval_at_depth<5>(rec, k, cur, gpb, gl);
+    case 0: return eval_at_depth<0>(rec, k, cur, gpb, gl, nib);
+    case 1: return eval_at_depth<1>(rec, k, cur, gpb, gl, nib);
+    case 2: return eval_at_depth<2>(rec, k, cur, gpb, gl, nib);
+    case 3: return eval_at_depth<3>(rec, k, cur, gpb, gl, nib);
+    case 4: return eval_at_depth<4>(rec, k, cur, gpb, gl, nib);
+    default: return eval_at_depth<5>(rec, k, cur, gpb, gl, nib);
   }
 }
 
@@ -242,11 +270,11 @@ __device__ __forceinline__ void step_item(const RoundKeys &rk, uint32_t P32, con
       const uint4 tr = wide ? make_uint4(0u, 0u, 0u, 0u) : rec;
       const int kt = wide ? 0 : k;
       const int K = __reduce_max_sync(kFull, (unsigned)kt);
-      if (__any_sync(kFull, has && !wide)) fword |= (wide ? 0u : my_sel) & eval_uniform(K, tr, kt, c.cur, c.gpb, c.gl);
+      if (__any_sync(kFull, has && !wide)) fword |= (wide ? 0u : my_sel) & eval_uniform(K, tr, kt, c.cur, c.gpb, c.gl, c.nib);
       if (wide) fword |= eval_wide_lanes<KMAX>(rec, my_sel, c.cur, c.gpb, c.gl, c.wide_tt, c.wide_par);
     } else {
       const int K = __reduce_max_sync(kFull, (unsigned)k);
-      if (__any_sync(kFull, has)) fword |= my_sel & eval_uniform(K, rec, k, c.cur, c.gpb, c.gl);
+      if (__any_sync(kFull, has)) fword |= my_sel & eval_uniform(K, rec, k, c.cur, c.gpb, c.gl, c.nib);
     }
   }
 #pragma unroll
