@@ -50,13 +50,13 @@ typedef enum pbn_status {
     PBN_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up */
     PBN_ERR_NOT_CONVERGED = 5,  /* a stopping rule was not met within the length cap */
     PBN_ERR_INSUFFICIENT = 6,   /* the window cannot give alpha and beta (no 0->1 or 1->0) */
-    PBN_ERR_UNSUPPORTED = 7,    /* valid input beyond this build's limits */
+    PBN_ERR_UNSUPPORTED = 7,    /* valid input beyond the library's limits */
     PBN_ERR_CANCELLED = 8       /* an engine query withdrawn by pbn_engine_cancel */
 } pbn_status;
 
 enum { PBN_PERTURB_PER_NODE = 0, PBN_PERTURB_GLOBAL = 1 };
 
-/* Limits of this build. */
+/* Limits of this library. */
 #define PBN_MAX_NODES 4096          /* node ids are 12-bit in the device tables */
 #define PBN_MAX_PARENTS 15          /* truth tables up to 32768 bits (1024 words) */
 #define PBN_MAX_FUNCTIONS_PER_NODE 16

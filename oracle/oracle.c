@@ -1009,7 +1009,7 @@ static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
  * (skewness threshold 4 giving batch size 16, randomness-test size 0.20,
  * largest spacer 10, batch-size factor sqrt 2 with a 10% batch-count cut when
  * the largest spacer fails, at most max(1024, current) batches when the CI is
- * too wide) are placeholders of this build, not verified against that
+ * too wide) are placeholders of this implementation, not verified against that
  * reference: parity between the two implementations holds, agreement with the
  * reference's Skart does not.
  */
@@ -1105,7 +1105,7 @@ done:
 
 /*
  * Alg. 2 (Sec. 3.2), the sequential Skart method on chain 0 of the seed's
- * family, with the constants of this build's Alg. 4 (placeholders for the
+ * family, with the constants of this oracle's Alg. 4 (placeholders for the
  * Skart reference, see orc_estimate_skart):
  *  - eta = 1280 samples; skewness of the last 1024 gives the batch size
  *    (16 when |skewness| > 4, else 1); p := eta batches, eta := kappa p;

@@ -662,7 +662,7 @@ const char *pbn_status_string(int status) {
     case PBN_ERR_TIMEOUT: return "device wait timed out";
     case PBN_ERR_NOT_CONVERGED: return "not converged within the length cap";
     case PBN_ERR_INSUFFICIENT: return "window cannot give alpha and beta";
-    case PBN_ERR_UNSUPPORTED: return "unsupported by this build";
+    case PBN_ERR_UNSUPPORTED: return "unsupported by this library";
     case PBN_ERR_CANCELLED: return "cancelled";
     default: return "unknown status";
   }
